@@ -1,0 +1,243 @@
+"""Plain FP64 CPU oracle for the synthetic-visibility / chi-square hot path
+of GALARIO (Tazzari, Beaujean & Testi, arXiv 1709.06999).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, obviously correct
+restatement of the method that the CUDA library is checked against.  Only the
+test-suite, the package smoke check and the benchmark's CPU-baseline leg may
+import it; the library itself never calls it, and it shares no code, table or
+helper with the CUDA path.
+
+Everything is computed in float64 with numpy.  Two library primitives serve
+as steps: ``numpy.fft.rfft2`` (the 2D real-to-complex FFT of Sect. 4) and
+``numpy.interp`` (the 1D linear interpolation of the radial profile used in
+App. D).  Every other step is written out in the order of App. D:
+
+    sweep (profile -> image)           Sect. 2 "Basic usage", Sect. 4, App. D
+    fftshift -> rfft2 -> fftshift(0)   Sect. 4 (shift, FFT, shift), App. D
+    rotate (u, v) by PA                Sect. 3.2, rotation equations
+    uv -> grid index, Hermitian fold   App. D (indices, negative-u mapping)
+    bilinear interpolation             end of Sect. 3.3 (Press et al.)
+    translate by (dRA, dDec)           Sect. 3.2 + App. D (phase factor)
+    chi-square                         Sect. 3.1, Eq. (chap6.eq:def.chi.square)
+
+Readings of points the paper leaves open or states inconsistently are listed
+in the design notes; the ones that change arithmetic are repeated in the
+docstrings below.  Pins: every function here is checked, on the CPU, against
+something other than itself (brute-force DFT, closed-form transforms,
+invariants) in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "pixel_coordinates",
+    "sweep",
+    "half_spectrum",
+    "rotate_uv",
+    "uv_to_index",
+    "bilinear",
+    "sample_spectrum",
+    "sample_image",
+    "sample_profile",
+    "chi2",
+    "chi2_image",
+    "chi2_profile",
+    "uv_extent",
+]
+
+
+def pixel_coordinates(nxy: int, dxy: float):
+    """Sky offsets of the pixel centres of an nxy x nxy image (radians).
+
+    Column j sits at x_j = (nxy/2 - j) * dxy and row i at y_i = (nxy/2 - i) *
+    dxy: East is to the left, North to the top, and the origin (l, m) = (0, 0)
+    is the centre pixel (nxy/2, nxy/2).  Sect. 2 (image orientation), Sect.
+    3.3 (origin at the image centre), App. D (mesh-grid construction).
+    """
+    half = nxy // 2
+    idx = np.arange(nxy, dtype=np.float64)
+    x = (half - idx) * dxy
+    y = (half - idx) * dxy
+    return x, y
+
+
+def sweep(intensity, Rmin: float, dR: float, nxy: int, dxy: float, inc: float = 0.0):
+    """Image (Jy/pixel) of an axisymmetric profile I(r) (Jy/sr) seen at inclination inc.
+
+    Sect. 2 (sampleProfile: azimuthal sweep of I(r) over 2*pi, inclination
+    along the line of sight) and App. D (py_chi2Profile).  Steps:
+
+    1. radial nodes r_n = Rmin + n * dR, n = 0 .. nr-1;
+    2. pixel radius r_ij = sqrt((x_j / cos(inc))**2 + y_i**2): the East-West
+       axis is stretched by 1/cos(inc), i.e. the disc is tilted about the
+       North-South axis (Fig. 2 caption);
+    3. 1D *linear* interpolation of I at r_ij, zero outside [r_0, r_{nr-1}]
+       (App. D uses interp1d(kind='linear', fill_value=0)); the text's
+       "bilinear as in Press" is read as this 1D interpolation;
+    4. Jy/sr -> Jy/pixel by multiplying with dxy**2 (App. D);
+    5. the centre pixel takes the linear extrapolation of the first two
+       profile samples to r = 0 (App. D, f_center).
+
+    The input array is not modified (App. D scales it in place; the library
+    must not, and neither does this oracle).
+    """
+    I = np.asarray(intensity, dtype=np.float64)
+    nr = I.shape[0]
+    if nr < 2:
+        raise ValueError("profile needs at least two samples")
+    radii = Rmin + dR * np.arange(nr, dtype=np.float64)
+    x, y = pixel_coordinates(nxy, dxy)
+    xs = x / math.cos(inc)
+    r = np.sqrt(xs[None, :] ** 2 + y[:, None] ** 2)
+    img = np.interp(r, radii, I, left=0.0, right=0.0)
+    img *= dxy * dxy
+    slope = (I[1] - I[0]) / (radii[1] - radii[0])
+    centre = I[0] + slope * (0.0 - radii[0])
+    img[nxy // 2, nxy // 2] = centre * dxy * dxy
+    return img
+
+
+def half_spectrum(image):
+    """Half-plane spectrum G of a real nxy x nxy image, origin-centred on both sides.
+
+    Sect. 4: the image origin is at the centre pixel while the FFT expects it
+    at [0, 0], so the image is shifted, transformed real-to-complex and the
+    result is shifted back along the v axis (App. D: fftshift, rfft2,
+    fftshift over axis 0).  Unnormalised forward transform e^{-2 pi i k n / N}.
+    G has nxy rows (v; row nxy/2 is v = 0) and nxy/2 + 1 columns (u >= 0);
+    cell (r, c) is the visibility at u = c * du, v = (r - nxy/2) * du with
+    du = 1 / (nxy * dxy).
+    """
+    img = np.asarray(image, dtype=np.float64)
+    n0, n1 = img.shape
+    if n0 != n1 or n0 % 2:
+        raise ValueError("image must be square with an even side")
+    centred = np.fft.fftshift(img)
+    return np.fft.fftshift(np.fft.rfft2(centred), axes=0)
+
+
+def rotate_uv(u, v, PA: float):
+    """(u', v') = rotation of the uv points used for a model at position angle PA.
+
+    Sect. 3.2: u' = u cos PA - v sin PA, v' = u sin PA + v cos PA (the
+    equations are taken literally; the text calls this a rotation by -PA).
+    """
+    c, s = math.cos(PA), math.sin(PA)
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    return u * c - v * s, u * s + v * c
+
+
+def uv_to_index(urot, vrot, nxy: int, dxy: float):
+    """Fractional grid indices (row iv, column iu) of rotated uv points, and the fold mask.
+
+    App. D: du = 1 / (nxy * dxy); iu = |u'| / du; iv = nxy/2 + v'/du, except
+    that points with u' < 0 (strictly) use the Hermitian partner (-u', -v'),
+    i.e. iv = nxy/2 - v'/du, and their sampled value is conjugated.
+    """
+    du = 1.0 / (nxy * dxy)
+    neg = urot < 0.0
+    iu = np.abs(urot) / du
+    iv = nxy / 2.0 + np.where(neg, -vrot, vrot) / du
+    return iv, iu, neg
+
+
+def bilinear(grid, iv, iu):
+    """Bilinear interpolation of a node grid at fractional (row, column) positions.
+
+    End of Sect. 3.3 (Press et al.): the value at a point is inferred from the
+    four closest grid nodes assuming linear variation along each axis.  App. D
+    performs this with a degree-1, zero-smoothing spline on the nodes
+    0..nrow-1, 0..ncol-1, which evaluates arguments beyond the node range at
+    the range edge; the same clamping is applied here.  The cell is
+    (floor(idx), floor(idx) + 1) except at the last node, where the last cell
+    is used with fraction 1.
+    """
+    G = np.asarray(grid)
+    nrow, ncol = G.shape
+    fv = np.clip(np.asarray(iv, dtype=np.float64), 0.0, nrow - 1.0)
+    fu = np.clip(np.asarray(iu, dtype=np.float64), 0.0, ncol - 1.0)
+    r0 = np.minimum(np.floor(fv), nrow - 2).astype(np.int64)
+    c0 = np.minimum(np.floor(fu), ncol - 2).astype(np.int64)
+    tv = fv - r0
+    tu = fu - c0
+    return ((1.0 - tv) * (1.0 - tu) * G[r0, c0]
+            + (1.0 - tv) * tu * G[r0, c0 + 1]
+            + tv * (1.0 - tu) * G[r0 + 1, c0]
+            + tv * tu * G[r0 + 1, c0 + 1])
+
+
+def sample_spectrum(G, nxy: int, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0,
+                    PA: float = 0.0):
+    """Visibilities at (u, v) from a half spectrum G: rotate, index, interpolate, translate.
+
+    Sect. 3.2 and App. D.  The offsets are rotated with the same matrix as the
+    uv points and the phase factor is exp(+i theta) with
+    theta = 2 pi (u' dRA' + v' dDec').  The text writes the factor with a
+    minus sign; App. D (and the orientation of its pixel grid) fix the plus
+    sign, under which a source moved East by dRA acquires exp(+2 pi i u dRA).
+    """
+    urot, vrot = rotate_uv(u, v, PA)
+    c, s = math.cos(PA), math.sin(PA)
+    dRA_rot = 2.0 * math.pi * (dRA * c - dDec * s)
+    dDec_rot = 2.0 * math.pi * (dRA * s + dDec * c)
+    iv, iu, neg = uv_to_index(urot, vrot, nxy, dxy)
+    vis = bilinear(G, iv, iu)
+    vis = np.where(neg, np.conj(vis), vis)
+    theta = urot * dRA_rot + vrot * dDec_rot
+    return vis * (np.cos(theta) + 1j * np.sin(theta))
+
+
+def sample_image(image, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0):
+    """Synthetic visibilities (Jy) of a model image (Jy/pixel) at uv points (wavelengths).
+
+    Sect. 2 (sampleImage) and Fig. 3: shift, FFT, shift, then sampling.
+    """
+    img = np.asarray(image, dtype=np.float64)
+    return sample_spectrum(half_spectrum(img), img.shape[0], dxy, u, v, dRA, dDec, PA)
+
+
+def sample_profile(intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v,
+                   dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0):
+    """Synthetic visibilities of an axisymmetric profile: sweep, then sample_image (Sect. 2, Fig. 3)."""
+    img = sweep(intensity, Rmin, dR, nxy, dxy, inc)
+    return sample_image(img, dxy, u, v, dRA, dDec, PA)
+
+
+def chi2(vis, re_obs, im_obs, w):
+    """Weighted chi-square of Eq. (chap6.eq:def.chi.square), Sect. 3.1.
+
+    chi2 = sum_k w_k [(Re_obs - Re_mod)^2 + (Im_obs - Im_mod)^2].  The terms are
+    formed in float64 and summed with ``math.fsum`` (Shewchuk's exact
+    summation), so the sum itself adds no rounding beyond the final one.
+    """
+    vis = np.asarray(vis)
+    dr = np.asarray(re_obs, dtype=np.float64) - vis.real
+    di = np.asarray(im_obs, dtype=np.float64) - vis.imag
+    terms = np.asarray(w, dtype=np.float64) * (dr * dr + di * di)
+    return math.fsum(terms.tolist())
+
+
+def chi2_image(image, dxy: float, u, v, re_obs, im_obs, w, dRA: float = 0.0, dDec: float = 0.0,
+               PA: float = 0.0):
+    """chi2Image of Sect. 2: sample_image followed by the chi-square reduction."""
+    return chi2(sample_image(image, dxy, u, v, dRA, dDec, PA), re_obs, im_obs, w)
+
+
+def chi2_profile(intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v, re_obs, im_obs, w,
+                 dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0):
+    """chi2Profile of Sect. 2: sample_profile followed by the chi-square reduction."""
+    vis = sample_profile(intensity, Rmin, dR, nxy, dxy, u, v, dRA, dDec, PA, inc)
+    return chi2(vis, re_obs, im_obs, w)
+
+
+def uv_extent(u, v):
+    """Largest baseline length max_k sqrt(u_k^2 + v_k^2) (Sect. 3.3, criterion (i))."""
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    if u.size == 0:
+        return 0.0
+    return float(np.sqrt(np.max(u * u + v * v)))
