@@ -1,0 +1,384 @@
+"""Throughput benchmark of the chi-square hot path on one or more GB300s.
+
+Workload (one "step" = one full chi2_image evaluation: row FFT, pruned column
+FFT, gather + phase + chi-square): nxy = 4096 float32 image of three random
+elliptical Gaussians plus an exp(-r/0.2") disc, dxy = 0.002", M = 5e6
+ALMA-like uv points (43 antennas, 60 hour angles, 93 channels around 100 GHz),
+random dRA/dDec in +-0.1" and PA in [0, pi).  Inputs are resident in HBM; L2
+is flushed (a 256 MiB write) before every timed step; each step is timed on
+the device with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank evaluates its own replica of the workload (the steps
+are independent evaluations, as in an MCMC batch): weak scaling, no
+collective on the data path; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "chi2_image evals/s at nxy=4096, Nuv=5e6 (FP32 bulk, FP64 reduction)"
+UNIT = "evals/s"
+WORKLOAD = "chi2_image nxy=4096 dxy=0.002as M=5e6 ALMA-like uv, 3 Gaussians + exp disc"
+NXY, M_UV = 4096, 5_000_000
+L2_FLUSH_BYTES = 256 << 20
+STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
+KERNELS = {1: "row_pass_kernel<float,false>", 2: "col_pass_kernel<float>",
+           3: "gather_kernel<float,true>"}
+
+
+def algorithmic_bytes(stage: int, nxy: int, M: int, Kc: int, nrw: int) -> float:
+    """Compulsory DRAM bytes of one launch of a stage (float32 path).
+
+    row FFT:   read the image (4 N^2) + write the kept columns (8 N Kc)
+    col FFT:   read the kept columns (8 N Kc) + write the window (8 nrw Kc)
+    gather:    read u, v, Re, Im, w (20 B per point); the window (8 nrw Kc)
+               is read once from DRAM and then served from cache
+    """
+    if stage == 1:
+        return 4.0 * nxy * nxy + 8.0 * nxy * Kc
+    if stage == 2:
+        return 8.0 * nxy * Kc + 8.0 * nrw * Kc
+    if stage == 3:
+        return 20.0 * M + 8.0 * nrw * Kc
+    return 8.0 * M
+
+
+def window(rho: float, S: float, N: int):
+    """Kept spectrum window (same rule as the library's pruning)."""
+    P = N // 2 + 1
+    e = rho * S
+    if not e < N:
+        return P, N
+    k = math.floor(e) + 3
+    lo, hi = max(0, N // 2 - k), min(N - 1, N // 2 + k)
+    return min(k + 1, P), hi - lo + 1
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1709_06999_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernels
+    have not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    k = rec.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_eval(p, re, im):
+    import oracle
+    return oracle.chi2_image(p.image, p.dxy, p.u, p.v, re, im, p.w, p.dRA, p.dDec, p.PA)
+
+
+def make_problem(seed: int = 2):
+    from paper_1709_06999_gb300 import synth
+    p = synth.large_image_problem(nxy=NXY, M=M_UV, seed=seed)
+    p.image = p.image.astype(np.float32).astype(np.float64)
+    for k in ("u", "v", "w", "noise_re", "noise_im"):
+        setattr(p, k, getattr(p, k).astype(np.float32).astype(np.float64))
+    return p
+
+
+def cpu_baseline(p, re, im, evals: int):
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        oracle_eval(p, re, im)
+    dt = time.perf_counter() - t0
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{evals} full FP64 oracle chi2_image evaluation(s) of the same workload "
+                      f"(numpy, single thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    p = make_problem()
+    rng = np.random.default_rng(7)
+    re = rng.standard_normal(p.u.size)
+    im = rng.standard_normal(p.u.size)
+    for _ in range(args.warmup):
+        oracle_eval(p, re, im)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_eval(p, re, im)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full FP64 oracle evaluations (numpy, 1 thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1709_06999_gb300 import Context
+
+    p = make_problem(seed=2 + rank)
+    ctx = Context(dev.index)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    img = d(p.image)
+    u, v, w = d(p.u), d(p.v), d(p.w)
+    # observed data = model (from this library) + noise: inputs for timing only
+    model = ctx.sample_image(img, p.dxy, u, v, p.dRA, p.dDec, p.PA)
+    re = (model[:, 0] + d(p.noise_re)).contiguous()
+    im = (model[:, 1] + d(p.noise_im)).contiguous()
+    obs = ctx.register(u, v, re, im, w)
+    out = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # a few parameter sets, as successive MCMC steps would use
+    prng = np.random.default_rng(11 + rank)
+    params = [(float(a), float(b), float(c)) for a, b, c in
+              zip(prng.uniform(-0.1, 0.1, 8) * math.pi / 648000,
+                  prng.uniform(-0.1, 0.1, 8) * math.pi / 648000, prng.uniform(0, math.pi, 8))]
+
+    def step(i):
+        dRA, dDec, PA = params[i % len(params)]
+        ctx.chi2_image(img, p.dxy, obs, dRA, dDec, PA, out=out)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launch_count()
+    ctx.set_stage_timing(True)
+    with ClockSampler(dev.index if world == 1 else local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+    stage = ctx.stage_times()
+    ctx.set_stage_timing(False)
+    gpu_launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * 1000.0 / ms_per_step
+
+    # end to end through the C ABI with host buffers: H2D of the step's image
+    # from pinned memory, compute, D2H of chi2, synchronise
+    img_host = torch.as_tensor(p.image, dtype=torch.float32).pin_memory()
+    for i in range(2):
+        ctx.chi2_image_host(img_host, p.dxy, obs, *params[i])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_steps = max(3, min(args.steps, 50))
+    for i in range(e2e_steps):
+        ctx.chi2_image_host(img_host, p.dxy, obs, *params[i % len(params)])
+    e2e_dt = time.perf_counter() - t0
+    e2e_value = world * e2e_steps / e2e_dt
+
+    # plain FP64 single-call path on the same workload (context)
+    d64 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)  # noqa: E731
+    obs64 = ctx.register(d64(p.u), d64(p.v), re.double(), im.double(), d64(p.w))
+    img64 = d64(p.image)
+    ctx.chi2_image(img64, p.dxy, obs64, *params[0], out=out)
+    torch.cuda.synchronize(dev)
+    s64, e64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n64 = 5
+    s64.record(stream)
+    for i in range(n64):
+        ctx.chi2_image(img64, p.dxy, obs64, *params[i % len(params)], out=out)
+    e64.record(stream)
+    torch.cuda.synchronize(dev)
+    ms64 = s64.elapsed_time(e64) / n64
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest average launch time)
+    rho = float(np.sqrt(np.max(p.u ** 2 + p.v ** 2)))
+    Kc, nrw = window(rho, NXY * p.dxy, NXY)
+    avg = {s: (stage[s][0] / stage[s][1]) for s in (1, 2, 3) if stage[s][1]}
+    dom = max(avg, key=avg.get)
+    alg = algorithmic_bytes(dom, NXY, M_UV, Kc, nrw)
+    achieved = alg / (avg[dom] * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = measured_traffic(KERNELS[dom])
+
+    base = None
+    if world == 1 and args.cpu_evals > 0:
+        base = cpu_baseline(p, re.double().cpu().numpy(), im.double().cpu().numpy(),
+                            evals=args.cpu_evals)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV, "l2": "flushed before every step",
+                   "kept_window": {"columns": Kc, "rows": nrw}, "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * NXY * NXY,
+                "d2h_bytes_per_step": 8,
+                "note": "host image (pinned) -> device, chi2 -> host, per step; observation resident"},
+        "gpu_launches": gpu_launches,
+        "roofline": {"bound": "hbm", "kernel": KERNELS[dom], "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": alg,
+                     "avg_launch_us": 1000 * avg[dom]},
+        "stages_us": {STAGES[s]: round(1000 * stage[s][0] / stage[s][1], 2)
+                      for s in range(4) if stage[s][1]},
+        "fp64_plain": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                       "note": "same workload through the float64 entry point, single calls"},
+        "clocks": clk.summary(),
+    }
+    if base is not None:
+        line["cpu_baseline"] = base
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-evals", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # the timing rules need at least 3 warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,171 @@
+/*
+ * galario_gb300.h -- C ABI of the GB300 (sm_103a) visibility / chi-square library.
+ *
+ * The library computes synthetic interferometric visibilities of a model image,
+ * or of an axisymmetric radial profile swept into an image, at a set of uv
+ * points, and their weighted chi-square against observed visibilities: the hot
+ * path of GALARIO (Tazzari, Beaujean & Testi, arXiv 1709.06999).  Every step
+ * runs in hand-written CUDA kernels; this header is the whole public surface.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Units (Sect. 2 "Basic usage"): images are in Jy/pixel, profiles in Jy/sr,
+ *   u and v in wavelengths; dxy, Rmin, dR, dRA, dDec, PA and inc in radians.
+ *   Geometry scalars are `double` in both precisions.
+ * Image layout (Sect. 2, Sect. 3.3): nxy x nxy, row-major, row 0 at the top
+ *   (North), column 0 at the left (East); the origin is the centre pixel
+ *   (nxy/2, nxy/2).  nxy must be a power of two with 4 <= nxy <= 8192.
+ * Visibility output: interleaved (Re, Im) pairs, 2*M values of the entry
+ *   point's precision.
+ * Pointers: unless a name ends in `_host`, every array argument is DEVICE
+ *   memory on the context's device, owned by the caller, borrowed for the
+ *   duration of the stream-ordered work; inputs are never modified.  Arrays of
+ *   the _f32 entry points must be 4-byte aligned, of the _f64 ones 8-byte
+ *   aligned (16-byte alignment enables vector loads).
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Entry points only enqueue work; they do not synchronise unless
+ *   documented (the `_host` variants do).  A context must be used by one host
+ *   thread and one stream at a time: its workspace is shared by its calls.
+ * Errors: every int-returning call returns GAL_OK (0) or a negative GAL_E_*
+ *   code; gal_strerror() names it.  On error nothing has been enqueued, except
+ *   for GAL_E_CUDA, which reports a failed CUDA call (the message of the last
+ *   CUDA error is kept in the context, see gal_last_cuda_error()).
+ * Off-grid uv points: a point whose grid index lies beyond the half spectrum
+ *   is evaluated at the nearest edge node, as the App. D reference does.
+ * First use of a size: the first call with a new nxy (per precision) allocates
+ *   workspace and twiddle tables.  gal_reserve() performs that allocation up
+ *   front; after it, calls allocate nothing and may be captured in a CUDA graph.
+ */
+#ifndef GALARIO_GB300_H
+#define GALARIO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GAL_OK          0
+#define GAL_E_INVAL    -1   /* bad argument: null pointer, nxy not a power of two in [4, 8192],
+                               nr < 2, dR <= 0, dxy <= 0, |inc| >= pi/2, M < 0, misaligned array */
+#define GAL_E_NOMEM    -2   /* device allocation failed */
+#define GAL_E_CUDA     -3   /* a CUDA runtime call failed */
+#define GAL_E_RANGE    -4   /* internal index check tripped (see gal_check) */
+#define GAL_E_DEVICE   -5   /* no usable CUDA device / wrong architecture */
+
+typedef struct gal_ctx gal_ctx;     /* workspace, twiddle tables, launch shapes, counters */
+typedef struct gal_data gal_data;   /* a registered observation: u, v, Re, Im, w + uv extent */
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (made current for the call).  Owns all
+ * library workspace.  Returns GAL_E_DEVICE if the device is absent. */
+int gal_create(gal_ctx** out, int device);
+/* Free the context and all workspace.  Waits for the device.  NULL is ignored. */
+void gal_destroy(gal_ctx* ctx);
+/* Pre-allocate workspace and twiddles for images up to `nxy` in precision
+ * `real_bytes` (4 or 8), so that later calls allocate nothing. */
+int gal_reserve(gal_ctx* ctx, int nxy, int real_bytes);
+/* Name of a status code. */
+const char* gal_strerror(int status);
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* gal_last_cuda_error(const gal_ctx* ctx);
+/* Synchronise the device and report whether any kernel's internal index check
+ * tripped since the last gal_check (GAL_E_RANGE) -- it never should. */
+int gal_check(gal_ctx* ctx);
+/* Number of kernels this context has launched since creation. */
+uint64_t gal_launch_count(const gal_ctx* ctx);
+/* Per-stage device timing.  When enabled, each call brackets its kernels with
+ * CUDA events; gal_stage_times synchronises and returns, per stage, the summed
+ * milliseconds and the number of launches since timing was (re)enabled.
+ * Stages: 0 uv extent, 1 row FFT (with sweep), 2 column FFT, 3 sample/chi2. */
+int gal_set_stage_timing(gal_ctx* ctx, int enable);
+int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4);
+
+/* ---- observations ------------------------------------------------------------------- */
+
+/* Register an observation of M visibilities: u, v (wavelengths), Re_obs, Im_obs (Jy)
+ * and weights w = 1/sigma^2 (Sect. 3.1, Eq. chap6.eq:def.chi.square).  The arrays
+ * are borrowed (device memory, must outlive the handle).  Enqueues on `stream` one
+ * reduction for the largest baseline sqrt(u^2+v^2) (Sect. 3.3, criterion (i)),
+ * which later calls use to restrict the FFT to the part of the spectrum the uv
+ * points can reach (an exact pruning). */
+int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
+                        const float* im, const float* w, int64_t M, void* stream, gal_data** out);
+int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
+                        const double* im, const double* w, int64_t M, void* stream, gal_data** out);
+/* Release a handle (not the borrowed arrays).  Waits for the device. */
+void gal_data_destroy(gal_data* data);
+
+/* ---- the operations of Fig. 3 --------------------------------------------------------- */
+
+/* sweep: image_out[nxy*nxy] (Jy/pixel) of the profile I[nr] (Jy/sr) sampled at radii
+ * Rmin + k*dR, swept over 2*pi and inclined by `inc` about the North-South axis
+ * (Sect. 2 sampleProfile, Sect. 4 "sweep", App. D): linear interpolation in r,
+ * zero outside [Rmin, Rmin + (nr-1) dR], centre pixel linearly extrapolated to
+ * r = 0, multiplied by dxy^2. */
+int gal_sweep_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                  double dxy, double inc, float* image_out, void* stream);
+int gal_sweep_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                  double dxy, double inc, double* image_out, void* stream);
+
+/* sampleImage (Sect. 2, Fig. 3): visibilities of `image` at the M points (u, v),
+ * with the model rotated by PA and shifted by (dRA, dDec) (Sect. 3.2).  Steps:
+ * fftshift -> real-to-complex 2D FFT -> fftshift along v (Sect. 4), uv rotation,
+ * bilinear interpolation (Sect. 3.3), phase factor exp(+2 pi i (u dRA + v dDec))
+ * (App. D sign).  vis_out: 2*M values.  Computes the uv extent first (one extra
+ * read of u and v). */
+int gal_sample_image_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                         double dDec, double PA, int64_t M, const float* u, const float* v,
+                         float* vis_out, void* stream);
+int gal_sample_image_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                         double dDec, double PA, int64_t M, const double* u, const double* v,
+                         double* vis_out, void* stream);
+
+/* sampleProfile (Sect. 2, Fig. 3): as sample_image for the image that gal_sweep
+ * would produce; the sweep runs inside the row FFT, so no image is written. */
+int gal_sample_profile_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR,
+                           int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                           int64_t M, const float* u, const float* v, float* vis_out,
+                           void* stream);
+int gal_sample_profile_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR,
+                           int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                           int64_t M, const double* u, const double* v, double* vis_out,
+                           void* stream);
+
+/* chi2Image (Sect. 2, Eq. chap6.eq:def.chi.square): writes to *chi2_out (one
+ * double in device memory) sum_k w_k [(Re_k - Re_mod)^2 + (Im_k - Im_mod)^2] of
+ * the registered observation against the model image.  The reduction order is
+ * fixed, so repeated calls give bitwise identical results on one device.  The
+ * observation's precision must match the entry point's. */
+int gal_chi2_image_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                       double dDec, double PA, const gal_data* data, double* chi2_out,
+                       void* stream);
+int gal_chi2_image_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                       double dDec, double PA, const gal_data* data, double* chi2_out,
+                       void* stream);
+
+/* chi2Profile (Sect. 2): chi2_image of the swept profile (sweep fused into the FFT). */
+int gal_chi2_profile_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                         double dxy, double inc, double dRA, double dDec, double PA,
+                         const gal_data* data, double* chi2_out, void* stream);
+int gal_chi2_profile_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                         double dxy, double inc, double dRA, double dDec, double PA,
+                         const gal_data* data, double* chi2_out, void* stream);
+
+/* Host-buffer chi2Image (the paper's calling pattern, Sect. 4 "memory
+ * operations"): `image_host` (nxy*nxy values in host memory, ideally pinned) is
+ * copied to context workspace, chi2_image runs on `stream`, and the result is
+ * copied back to *chi2_host.  Synchronises `stream` before returning. */
+int gal_chi2_image_host_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,
+                            double dRA, double dDec, double PA, const gal_data* data,
+                            double* chi2_host, void* stream);
+int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, double dxy,
+                            double dRA, double dDec, double PA, const gal_data* data,
+                            double* chi2_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GALARIO_GB300_H */

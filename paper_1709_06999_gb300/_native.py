@@ -1,0 +1,61 @@
+"""ctypes declarations of the C ABI in include/galario_gb300.h.
+
+Loading fails loudly when the shared library is missing: there is no CPU
+fallback anywhere in the package.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgalario_gb300.so")
+
+P = ct.c_void_p
+I32 = ct.c_int
+I64 = ct.c_int64
+D = ct.c_double
+
+_SIGNATURES = {
+    "gal_create": (I32, [ct.POINTER(P), I32]),
+    "gal_destroy": (None, [P]),
+    "gal_reserve": (I32, [P, I32, I32]),
+    "gal_strerror": (ct.c_char_p, [I32]),
+    "gal_last_cuda_error": (ct.c_char_p, [P]),
+    "gal_check": (I32, [P]),
+    "gal_launch_count": (ct.c_uint64, [P]),
+    "gal_set_stage_timing": (I32, [P, I32]),
+    "gal_stage_times": (I32, [P, ct.POINTER(D), ct.POINTER(I64)]),
+    "gal_data_destroy": (None, [P]),
+}
+for _p in ("f32", "f64"):
+    _SIGNATURES.update({
+        f"gal_data_create_{_p}": (I32, [P, P, P, P, P, P, I64, P, ct.POINTER(P)]),
+        f"gal_sweep_{_p}": (I32, [P, P, I32, D, D, I32, D, D, P, P]),
+        f"gal_sample_image_{_p}": (I32, [P, P, I32, D, D, D, D, I64, P, P, P, P]),
+        f"gal_sample_profile_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, I64, P, P, P, P]),
+        f"gal_chi2_image_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
+        f"gal_chi2_profile_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, P, P, P]),
+        f"gal_chi2_image_host_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
+    })
+
+EXPORTED = sorted(_SIGNATURES)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ct.CDLL:
+    """Load the library (once) and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library not built: {path} is missing. Build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc).")
+    lib = ct.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,249 @@
+"""PyTorch-facing binding of the C ABI (argument marshalling only).
+
+Tensors must live on the context's CUDA device; float32 tensors select the
+``_f32`` entry points and float64 tensors the ``_f64`` ones.  Work is enqueued
+on the current torch stream of that device.  Every computation happens in the
+CUDA library; nothing here falls back to the CPU.
+
+Names follow the paper's functions (Sect. 2): sweep, sample_image,
+sample_profile, chi2_image, chi2_profile.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+
+import torch
+
+from . import _native
+
+_SUFFIX = {torch.float32: "f32", torch.float64: "f64"}
+
+
+class GalError(RuntimeError):
+    pass
+
+
+def _check(ctx_handle, status: int):
+    if status != 0:
+        lib = _native.load()
+        msg = lib.gal_strerror(status).decode()
+        if ctx_handle:
+            cu = lib.gal_last_cuda_error(ctx_handle).decode()
+            if cu:
+                msg += f" ({cu})"
+        raise GalError(f"galario_gb300 status {status}: {msg}")
+
+
+def _suffix(*tensors) -> str:
+    dt = tensors[0].dtype
+    if dt not in _SUFFIX:
+        raise TypeError(f"unsupported dtype {dt}; use float32 or float64")
+    for t in tensors[1:]:
+        if t.dtype != dt:
+            raise TypeError("all arrays of one call must share a dtype")
+    return _SUFFIX[dt]
+
+
+class Observation:
+    """A registered set of M visibilities (u, v, Re, Im, w) resident on the device.
+
+    Holds references to its tensors so that the borrowed device memory stays
+    alive.  Creation enqueues one reduction for the uv extent.
+    """
+
+    def __init__(self, ctx: "Context", u, v, re, im, w):
+        tensors = [ctx._dev(t) for t in (u, v, re, im, w)]
+        m = tensors[0].numel()
+        if any(t.numel() != m for t in tensors):
+            raise ValueError("u, v, re, im, w must have the same length")
+        self._tensors = tensors
+        self.ctx = ctx
+        self.M = m
+        self.dtype = tensors[0].dtype
+        sfx = _suffix(*tensors)
+        h = ct.c_void_p()
+        fn = getattr(ctx.lib, f"gal_data_create_{sfx}")
+        _check(ctx.handle, fn(ctx.handle, *[t.data_ptr() for t in tensors], m, ctx._stream(), ct.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.ctx.lib.gal_data_destroy(self.handle)
+            self.handle = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Owns the library workspace on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _native.load()
+        self.device = torch.device("cuda", device)
+        h = ct.c_void_p()
+        _check(None, self.lib.gal_create(ct.byref(h), device))
+        self.handle = h
+
+    # -- plumbing -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            self.lib.gal_destroy(self.handle)
+            self.handle = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _dev(self, t):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("expected a torch.Tensor")
+        if t.device != self.device:
+            raise ValueError(f"tensor on {t.device}, context on {self.device}")
+        return t.contiguous()
+
+    def reserve(self, nxy: int, dtype=torch.float32):
+        _check(self.handle, self.lib.gal_reserve(self.handle, nxy, 4 if dtype == torch.float32 else 8))
+
+    def check(self):
+        _check(self.handle, self.lib.gal_check(self.handle))
+
+    def launch_count(self) -> int:
+        return int(self.lib.gal_launch_count(self.handle))
+
+    def set_stage_timing(self, enable: bool):
+        _check(self.handle, self.lib.gal_set_stage_timing(self.handle, int(enable)))
+
+    def stage_times(self):
+        """Per stage (extent, row FFT, column FFT, sample/chi2): (total ms, launches)."""
+        ms = (ct.c_double * 4)()
+        n = (ct.c_int64 * 4)()
+        _check(self.handle, self.lib.gal_stage_times(self.handle, ms, n))
+        return [(ms[i], n[i]) for i in range(4)]
+
+    def register(self, u, v, re, im, w) -> Observation:
+        return Observation(self, u, v, re, im, w)
+
+    # -- operations ---------------------------------------------------------
+    def sweep(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float, inc: float = 0.0,
+              out=None):
+        I = self._dev(intensity)
+        sfx = _suffix(I)
+        if out is None:
+            out = torch.empty((nxy, nxy), dtype=I.dtype, device=self.device)
+        fn = getattr(self.lib, f"gal_sweep_{sfx}")
+        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc,
+                               out.data_ptr(), self._stream()))
+        return out
+
+    def sample_image(self, image, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0,
+                     PA: float = 0.0, out=None):
+        """Visibilities as an (M, 2) tensor of (Re, Im)."""
+        img, u, v = self._dev(image), self._dev(u), self._dev(v)
+        sfx = _suffix(img, u, v)
+        nxy = img.shape[0]
+        if img.dim() != 2 or img.shape[1] != nxy:
+            raise ValueError("image must be square")
+        m = u.numel()
+        if out is None:
+            out = torch.empty((m, 2), dtype=img.dtype, device=self.device)
+        fn = getattr(self.lib, f"gal_sample_image_{sfx}")
+        _check(self.handle, fn(self.handle, img.data_ptr(), nxy, dxy, dRA, dDec, PA, m,
+                               u.data_ptr(), v.data_ptr(), out.data_ptr(), self._stream()))
+        return out
+
+    def sample_profile(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v,
+                       inc: float = 0.0, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
+                       out=None):
+        I, u, v = self._dev(intensity), self._dev(u), self._dev(v)
+        sfx = _suffix(I, u, v)
+        m = u.numel()
+        if out is None:
+            out = torch.empty((m, 2), dtype=I.dtype, device=self.device)
+        fn = getattr(self.lib, f"gal_sample_profile_{sfx}")
+        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc,
+                               dRA, dDec, PA, m, u.data_ptr(), v.data_ptr(), out.data_ptr(),
+                               self._stream()))
+        return out
+
+    def chi2_image(self, image, dxy: float, obs: Observation, dRA: float = 0.0, dDec: float = 0.0,
+                   PA: float = 0.0, out=None):
+        """chi2 as a one-element float64 device tensor (stream-ordered, no sync)."""
+        img = self._dev(image)
+        sfx = _suffix(img)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        fn = getattr(self.lib, f"gal_chi2_image_{sfx}")
+        _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, dRA, dDec, PA,
+                               obs.handle, out.data_ptr(), self._stream()))
+        return out
+
+    def chi2_profile(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float,
+                     obs: Observation, inc: float = 0.0, dRA: float = 0.0, dDec: float = 0.0,
+                     PA: float = 0.0, out=None):
+        I = self._dev(intensity)
+        sfx = _suffix(I)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        fn = getattr(self.lib, f"gal_chi2_profile_{sfx}")
+        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc,
+                               dRA, dDec, PA, obs.handle, out.data_ptr(), self._stream()))
+        return out
+
+    def chi2_image_host(self, image_host, dxy: float, obs: Observation, dRA: float = 0.0,
+                        dDec: float = 0.0, PA: float = 0.0) -> float:
+        """chi2Image from a host (ideally pinned) image; copies in, computes, copies back."""
+        if image_host.device.type != "cpu":
+            raise ValueError("image_host must be a CPU tensor")
+        img = image_host.contiguous()
+        sfx = _suffix(img)
+        res = ct.c_double()
+        fn = getattr(self.lib, f"gal_chi2_image_host_{sfx}")
+        _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, dRA, dDec, PA,
+                               obs.handle, ct.byref(res), self._stream()))
+        return res.value
+
+
+_default: dict[int, Context] = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    d = torch.cuda.current_device() if device is None else device
+    if d not in _default:
+        _default[d] = Context(d)
+    return _default[d]
+
+
+# -- the paper's calling convention (Sect. 2), on the default context --------
+def sample_image(image, dxy, u, v, dRA=0.0, dDec=0.0, PA=0.0):
+    return default_context(image.device.index).sample_image(image, dxy, u, v, dRA, dDec, PA)
+
+
+def sample_profile(intensity, Rmin, dR, nxy, dxy, u, v, dRA=0.0, dDec=0.0, PA=0.0, inc=0.0):
+    return default_context(intensity.device.index).sample_profile(
+        intensity, Rmin, dR, nxy, dxy, u, v, inc, dRA, dDec, PA)
+
+
+def chi2_image(image, dxy, u, v, re, im, w, dRA=0.0, dDec=0.0, PA=0.0):
+    ctx = default_context(image.device.index)
+    obs = ctx.register(u, v, re, im, w)
+    return ctx.chi2_image(image, dxy, obs, dRA, dDec, PA)
+
+
+def chi2_profile(intensity, Rmin, dR, nxy, dxy, u, v, re, im, w, dRA=0.0, dDec=0.0, PA=0.0,
+                 inc=0.0):
+    ctx = default_context(intensity.device.index)
+    obs = ctx.register(u, v, re, im, w)
+    return ctx.chi2_profile(intensity, Rmin, dR, nxy, dxy, obs, inc, dRA, dDec, PA)
+
+
+def sweep(intensity, Rmin, dR, nxy, dxy, inc=0.0):
+    return default_context(intensity.device.index).sweep(intensity, Rmin, dR, nxy, dxy, inc)

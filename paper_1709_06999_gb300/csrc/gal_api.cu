@@ -1,0 +1,573 @@
+// C ABI of the library (declared in include/galario_gb300.h): context and
+// observation handles, argument checks, workspace management and the
+// sequencing of the kernels for each operation of Fig. 3 of the paper.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/galario_gb300.h"
+#include "gal_common.cuh"
+#include "gal_internal.h"
+
+namespace {
+
+constexpr int kMaxLog2 = 13;  // nxy <= 8192
+constexpr int kStages = 4;    // 0 extent, 1 row pass, 2 column pass, 3 gather
+
+struct TimedStage {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct gal_ctx {
+  int device = 0;
+  int num_sms = 0;
+  void* F1 = nullptr;  // row-pass output (nxy x Kc complex)
+  size_t F1_bytes = 0;
+  void* Gw = nullptr;  // pruned spectrum window (nrw x Kc complex)
+  size_t Gw_bytes = 0;
+  double* partials = nullptr;  // per-block chi2 partial sums
+  int partials_len = 0;
+  unsigned* counter = nullptr;  // last-block-done counter (self-resetting)
+  double* rho2 = nullptr;       // uv extent scratch for raw-pointer calls
+  int* err = nullptr;           // index-check flag
+  double* chi2_dev = nullptr;   // result slot for the host-buffer entry points
+  void* stage_img = nullptr;    // image staging for the host-buffer entry points
+  size_t stage_img_bytes = 0;
+  void* tw[2][kMaxLog2 + 1] = {};
+  int gather_blocks[2][2] = {};  // [f64?][chi2?]
+  int aux_blocks = 0;
+  uint64_t launches = 0;
+  bool timing = false;
+  std::vector<TimedStage> timed;
+  std::vector<cudaEvent_t> event_pool;
+  double stage_ms[kStages] = {};
+  int64_t stage_n[kStages] = {};
+  char last_err[256] = {0};
+};
+
+struct gal_data {
+  gal_ctx* ctx = nullptr;
+  int real_bytes = 0;
+  int64_t M = 0;
+  const void *u = nullptr, *v = nullptr, *re = nullptr, *im = nullptr, *w = nullptr;
+  double* rho2 = nullptr;  // device scalar: max(u^2 + v^2)
+};
+
+namespace {
+
+int cuda_fail(gal_ctx* ctx, cudaError_t e) {
+  if (ctx) snprintf(ctx->last_err, sizeof ctx->last_err, "%s", cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? GAL_E_NOMEM : GAL_E_CUDA;
+}
+
+#define GAL_CUDA(ctx, call)                      \
+  do {                                           \
+    cudaError_t _e = (call);                     \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e); \
+  } while (0)
+
+bool pow2_size(int n) { return n >= 4 && n <= (1 << kMaxLog2) && (n & (n - 1)) == 0; }
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+cudaError_t grow(void** p, size_t* have, size_t need) {
+  if (*have >= need) return cudaSuccess;
+  if (*p) {
+    cudaError_t e = cudaFree(*p);
+    if (e) return e;
+    *p = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(p, need);
+  if (e == cudaSuccess) *have = need;
+  return e;
+}
+
+template <typename T> constexpr int prec_index() { return sizeof(T) == 8 ? 1 : 0; }
+
+// Workspace and twiddles for images of side nxy in precision T.
+template <typename T> int ensure(gal_ctx* ctx, int nxy) {
+  using C = gal::cplx_t<T>;
+  const size_t spec = (size_t)nxy * (nxy / 2 + 1) * sizeof(C);
+  GAL_CUDA(ctx, grow(&ctx->F1, &ctx->F1_bytes, spec));
+  GAL_CUDA(ctx, grow(&ctx->Gw, &ctx->Gw_bytes, spec));
+  const int l = log2i(nxy);
+  void*& tw = ctx->tw[prec_index<T>()][l];
+  if (!tw) {
+    GAL_CUDA(ctx, cudaMalloc(&tw, (size_t)nxy * sizeof(C)));
+    GAL_CUDA(ctx, gal::Launch<T>::twiddles(tw, nxy, 0));
+    GAL_CUDA(ctx, cudaStreamSynchronize(0));
+    ctx->launches++;
+  }
+  return GAL_OK;
+}
+
+cudaEvent_t pool_event(gal_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void harvest(gal_ctx* ctx, size_t keep) {
+  // fold the oldest timed stages (all but `keep`) into the per-stage sums
+  if (ctx->timed.size() <= keep) return;
+  const size_t n = ctx->timed.size() - keep;
+  for (size_t i = 0; i < n; ++i) {
+    TimedStage& t = ctx->timed[i];
+    float ms = 0.f;
+    cudaEventSynchronize(t.b);
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      ctx->stage_ms[t.stage] += ms;
+      ctx->stage_n[t.stage] += 1;
+    }
+    ctx->event_pool.push_back(t.a);
+    ctx->event_pool.push_back(t.b);
+  }
+  ctx->timed.erase(ctx->timed.begin(), ctx->timed.begin() + n);
+}
+
+// Launch wrapper: counts the launch and, when timing, brackets it with events.
+template <typename F> int stage(gal_ctx* ctx, int id, cudaStream_t st, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ctx->timing) {
+    if (ctx->timed.size() > 8192) harvest(ctx, 4096);
+    a = pool_event(ctx);
+    b = pool_event(ctx);
+    cudaEventRecord(a, st);
+  }
+  cudaError_t e = launch();
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  ctx->launches++;
+  if (ctx->timing) {
+    cudaEventRecord(b, st);
+    ctx->timed.push_back({id, a, b});
+  }
+  return GAL_OK;
+}
+
+#define GAL_TRY(expr)            \
+  do {                           \
+    int _s = (expr);             \
+    if (_s != GAL_OK) return _s; \
+  } while (0)
+
+int check_geometry(int nxy, double dxy) {
+  if (!pow2_size(nxy)) return GAL_E_INVAL;
+  if (!(dxy > 0.0) || !std::isfinite(dxy)) return GAL_E_INVAL;
+  return GAL_OK;
+}
+
+int check_profile(const void* I, int nr, double Rmin, double dR, double inc) {
+  if (!I || nr < 2) return GAL_E_INVAL;
+  if (!(dR > 0.0) || !std::isfinite(dR) || !std::isfinite(Rmin)) return GAL_E_INVAL;
+  if (!(std::fabs(inc) < M_PI / 2)) return GAL_E_INVAL;
+  return GAL_OK;
+}
+
+gal::GatherParams gather_params(int nxy, double dxy, double dRA, double dDec, double PA) {
+  gal::GatherParams g;
+  g.cpa = std::cos(PA);
+  g.spa = std::sin(PA);
+  g.S = (double)nxy * dxy;
+  g.phx = dRA;
+  g.phy = dDec;
+  g.N = nxy;
+  return g;
+}
+
+// FFT of the image (or of the swept profile) into the pruned window ctx->Gw.
+template <typename T>
+int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
+             double dxy, const double* rho2, cudaStream_t st) {
+  GAL_TRY(ensure<T>(ctx, nxy));
+  const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
+  const double S = (double)nxy * dxy;
+  GAL_TRY(stage(ctx, 1, st, [&] {
+    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, st);
+  }));
+  GAL_TRY(stage(ctx, 2, st, [&] {
+    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, st);
+  }));
+  return GAL_OK;
+}
+
+template <typename T>
+int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
+                double dxy, double dRA, double dDec, double PA, int64_t M, const T* u,
+                const T* v, T* vis, cudaStream_t st) {
+  if (!ctx) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(nxy, dxy));
+  if (M < 0) return GAL_E_INVAL;
+  if (M == 0) return GAL_OK;
+  if (!u || !v || !vis) return GAL_E_INVAL;
+  if (!aligned(u, sizeof(T)) || !aligned(v, sizeof(T)) || !aligned(vis, 2 * sizeof(T)))
+    return GAL_E_INVAL;
+  GAL_TRY(stage(ctx, 0, st, [&] {
+    return gal::Launch<T>::extent(u, v, M, ctx->rho2, ctx->aux_blocks, st);
+  }));
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, ctx->rho2, st));
+  const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
+  const int blocks = ctx->gather_blocks[prec_index<T>()][0];
+  return stage(ctx, 3, st, [&] {
+    return gal::Launch<T>::gather(ctx->Gw, gp, ctx->rho2, u, v, nullptr, nullptr, nullptr, M,
+                                  vis, nullptr, nullptr, nullptr, ctx->err, blocks, st);
+  });
+}
+
+template <typename T>
+int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
+              double dxy, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
+              cudaStream_t st) {
+  if (!ctx || !d || !chi2) return GAL_E_INVAL;
+  if (d->ctx != ctx || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(nxy, dxy));
+  if (!aligned(chi2, sizeof(double))) return GAL_E_INVAL;
+  if (d->M == 0) {
+    GAL_CUDA(ctx, cudaMemsetAsync(chi2, 0, sizeof(double), st));
+    return GAL_OK;
+  }
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, st));
+  const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
+  const int blocks = ctx->gather_blocks[prec_index<T>()][1];
+  return stage(ctx, 3, st, [&] {
+    return gal::Launch<T>::gather(ctx->Gw, gp, d->rho2, static_cast<const T*>(d->u),
+                                  static_cast<const T*>(d->v), static_cast<const T*>(d->re),
+                                  static_cast<const T*>(d->im), static_cast<const T*>(d->w), d->M,
+                                  nullptr, ctx->partials, ctx->counter, chi2, ctx->err, blocks, st);
+  });
+}
+
+template <typename T>
+int sample_image_t(gal_ctx* ctx, const T* image, int nxy, double dxy, double dRA, double dDec,
+                   double PA, int64_t M, const T* u, const T* v, T* vis, void* stream) {
+  if (!image || !aligned(image, 2 * sizeof(T))) return GAL_E_INVAL;
+  gal::SweepParams sp{};
+  return sample_impl<T>(ctx, image, nullptr, sp, nxy, dxy, dRA, dDec, PA, M, u, v, vis,
+                        static_cast<cudaStream_t>(stream));
+}
+
+template <typename T>
+int sample_profile_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int nxy, double dxy,
+                     double inc, double dRA, double dDec, double PA, int64_t M, const T* u,
+                     const T* v, T* vis, void* stream) {
+  GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
+  if (!aligned(I, sizeof(T))) return GAL_E_INVAL;
+  gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
+  return sample_impl<T>(ctx, nullptr, I, sp, nxy, dxy, dRA, dDec, PA, M, u, v, vis,
+                        static_cast<cudaStream_t>(stream));
+}
+
+template <typename T>
+int chi2_image_t(gal_ctx* ctx, const T* image, int nxy, double dxy, double dRA, double dDec,
+                 double PA, const gal_data* d, double* chi2, void* stream) {
+  if (!image || !aligned(image, 2 * sizeof(T))) return GAL_E_INVAL;
+  gal::SweepParams sp{};
+  return chi2_impl<T>(ctx, image, nullptr, sp, nxy, dxy, dRA, dDec, PA, d, chi2,
+                      static_cast<cudaStream_t>(stream));
+}
+
+template <typename T>
+int chi2_profile_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int nxy, double dxy,
+                   double inc, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
+                   void* stream) {
+  GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
+  if (!aligned(I, sizeof(T))) return GAL_E_INVAL;
+  gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
+  return chi2_impl<T>(ctx, nullptr, I, sp, nxy, dxy, dRA, dDec, PA, d, chi2,
+                      static_cast<cudaStream_t>(stream));
+}
+
+template <typename T>
+int sweep_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int nxy, double dxy,
+            double inc, T* img, void* stream) {
+  if (!ctx || !img) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(nxy, dxy));
+  GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
+  if (!aligned(I, sizeof(T)) || !aligned(img, sizeof(T))) return GAL_E_INVAL;
+  gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return stage(ctx, 1, st, [&] {
+    return gal::Launch<T>::sweep(I, sp, nxy, img, ctx->aux_blocks, st);
+  });
+}
+
+template <typename T>
+int data_create_t(gal_ctx* ctx, const T* u, const T* v, const T* re, const T* im, const T* w,
+                  int64_t M, void* stream, gal_data** out) {
+  if (!ctx || !out || M < 0) return GAL_E_INVAL;
+  if (M > 0 && (!u || !v || !re || !im || !w)) return GAL_E_INVAL;
+  for (const void* p : {(const void*)u, (const void*)v, (const void*)re, (const void*)im,
+                        (const void*)w})
+    if (!aligned(p, sizeof(T))) return GAL_E_INVAL;
+  gal_data* d = new (std::nothrow) gal_data;
+  if (!d) return GAL_E_NOMEM;
+  d->ctx = ctx;
+  d->real_bytes = sizeof(T);
+  d->M = M;
+  d->u = u;
+  d->v = v;
+  d->re = re;
+  d->im = im;
+  d->w = w;
+  cudaError_t e = cudaMalloc(&d->rho2, sizeof(double));
+  if (e != cudaSuccess) {
+    delete d;
+    return cuda_fail(ctx, e);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int s = stage(ctx, 0, st, [&] {
+    return gal::Launch<T>::extent(u, v, M, d->rho2, ctx->aux_blocks, st);
+  });
+  if (s != GAL_OK) {
+    cudaFree(d->rho2);
+    delete d;
+    return s;
+  }
+  *out = d;
+  return GAL_OK;
+}
+
+template <typename T>
+int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, double dRA,
+                      double dDec, double PA, const gal_data* d, double* chi2_host, void* stream) {
+  if (!ctx || !image_host || !chi2_host) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(nxy, dxy));
+  const size_t bytes = (size_t)nxy * nxy * sizeof(T);
+  GAL_CUDA(ctx, grow(&ctx->stage_img, &ctx->stage_img_bytes, bytes));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GAL_CUDA(ctx, cudaMemcpyAsync(ctx->stage_img, image_host, bytes, cudaMemcpyHostToDevice, st));
+  GAL_TRY(chi2_image_t<T>(ctx, static_cast<const T*>(ctx->stage_img), nxy, dxy, dRA, dDec, PA, d,
+                          ctx->chi2_dev, stream));
+  GAL_CUDA(ctx, cudaMemcpyAsync(chi2_host, ctx->chi2_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                st));
+  GAL_CUDA(ctx, cudaStreamSynchronize(st));
+  return GAL_OK;
+}
+
+std::once_flag g_init_once;
+cudaError_t g_init_err = cudaSuccess;
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* gal_strerror(int s) {
+  switch (s) {
+    case GAL_OK: return "ok";
+    case GAL_E_INVAL: return "invalid argument";
+    case GAL_E_NOMEM: return "device allocation failed";
+    case GAL_E_CUDA: return "CUDA error";
+    case GAL_E_RANGE: return "internal index check tripped";
+    case GAL_E_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int gal_create(gal_ctx** out, int device) {
+  if (!out) return GAL_E_INVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GAL_E_DEVICE;
+  if (cudaSetDevice(device) != cudaSuccess) return GAL_E_DEVICE;
+  std::call_once(g_init_once, [] {
+    g_init_err = gal::Launch<float>::init();
+    if (g_init_err == cudaSuccess) g_init_err = gal::Launch<double>::init();
+  });
+  if (g_init_err != cudaSuccess) return GAL_E_DEVICE;  // e.g. no sm_103a image for this GPU
+  gal_ctx* ctx = new (std::nothrow) gal_ctx;
+  if (!ctx) return GAL_E_NOMEM;
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  ctx->gather_blocks[0][0] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(false);
+  ctx->gather_blocks[0][1] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(true);
+  ctx->gather_blocks[1][0] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(false);
+  ctx->gather_blocks[1][1] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(true);
+  ctx->aux_blocks = ctx->num_sms * 8;
+  int maxb = 0;
+  for (auto& a : ctx->gather_blocks)
+    for (int b : a) maxb = b > maxb ? b : maxb;
+  ctx->partials_len = maxb;
+  cudaError_t e = cudaSuccess;
+  if (!e) e = cudaMalloc(&ctx->partials, sizeof(double) * (size_t)maxb);
+  if (!e) e = cudaMalloc(&ctx->counter, sizeof(unsigned));
+  if (!e) e = cudaMalloc(&ctx->rho2, sizeof(double));
+  if (!e) e = cudaMalloc(&ctx->err, sizeof(int));
+  if (!e) e = cudaMalloc(&ctx->chi2_dev, sizeof(double));
+  if (!e) e = cudaMemset(ctx->counter, 0, sizeof(unsigned));
+  if (!e) e = cudaMemset(ctx->err, 0, sizeof(int));
+  if (!e) e = cudaDeviceSynchronize();
+  if (e) {
+    int s = cuda_fail(ctx, e);
+    gal_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return GAL_OK;
+}
+
+void gal_destroy(gal_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (void* p : {ctx->F1, ctx->Gw, (void*)ctx->partials, (void*)ctx->counter, (void*)ctx->rho2,
+                  (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img})
+    if (p) cudaFree(p);
+  for (auto& a : ctx->tw)
+    for (void* p : a)
+      if (p) cudaFree(p);
+  for (auto& t : ctx->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+int gal_reserve(gal_ctx* ctx, int nxy, int real_bytes) {
+  if (!ctx || !pow2_size(nxy)) return GAL_E_INVAL;
+  if (real_bytes == 4) return ensure<float>(ctx, nxy);
+  if (real_bytes == 8) return ensure<double>(ctx, nxy);
+  return GAL_E_INVAL;
+}
+
+const char* gal_last_cuda_error(const gal_ctx* ctx) { return ctx ? ctx->last_err : ""; }
+
+int gal_check(gal_ctx* ctx) {
+  if (!ctx) return GAL_E_INVAL;
+  GAL_CUDA(ctx, cudaDeviceSynchronize());
+  int flag = 0;
+  GAL_CUDA(ctx, cudaMemcpy(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
+  GAL_CUDA(ctx, cudaMemset(ctx->err, 0, sizeof(int)));
+  return flag ? GAL_E_RANGE : GAL_OK;
+}
+
+uint64_t gal_launch_count(const gal_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gal_set_stage_timing(gal_ctx* ctx, int enable) {
+  if (!ctx) return GAL_E_INVAL;
+  harvest(ctx, 0);
+  ctx->timing = enable != 0;
+  for (int s = 0; s < kStages; ++s) {
+    ctx->stage_ms[s] = 0.0;
+    ctx->stage_n[s] = 0;
+  }
+  return GAL_OK;
+}
+
+int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4) {
+  if (!ctx) return GAL_E_INVAL;
+  harvest(ctx, 0);
+  for (int s = 0; s < kStages; ++s) {
+    if (ms_out4) ms_out4[s] = ctx->stage_ms[s];
+    if (count_out4) count_out4[s] = ctx->stage_n[s];
+  }
+  return GAL_OK;
+}
+
+int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
+                        const float* im, const float* w, int64_t M, void* stream, gal_data** out) {
+  return data_create_t<float>(ctx, u, v, re, im, w, M, stream, out);
+}
+int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
+                        const double* im, const double* w, int64_t M, void* stream,
+                        gal_data** out) {
+  return data_create_t<double>(ctx, u, v, re, im, w, M, stream, out);
+}
+void gal_data_destroy(gal_data* d) {
+  if (!d) return;
+  cudaDeviceSynchronize();
+  if (d->rho2) cudaFree(d->rho2);
+  delete d;
+}
+
+int gal_sweep_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                  double dxy, double inc, float* image_out, void* stream) {
+  return sweep_t<float>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, image_out, stream);
+}
+int gal_sweep_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                  double dxy, double inc, double* image_out, void* stream) {
+  return sweep_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, image_out, stream);
+}
+
+int gal_sample_image_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                         double dDec, double PA, int64_t M, const float* u, const float* v,
+                         float* vis_out, void* stream) {
+  return sample_image_t<float>(ctx, image, nxy, dxy, dRA, dDec, PA, M, u, v, vis_out, stream);
+}
+int gal_sample_image_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                         double dDec, double PA, int64_t M, const double* u, const double* v,
+                         double* vis_out, void* stream) {
+  return sample_image_t<double>(ctx, image, nxy, dxy, dRA, dDec, PA, M, u, v, vis_out, stream);
+}
+
+int gal_sample_profile_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                           double dxy, double inc, double dRA, double dDec, double PA, int64_t M,
+                           const float* u, const float* v, float* vis_out, void* stream) {
+  return sample_profile_t<float>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, M, u, v,
+                                 vis_out, stream);
+}
+int gal_sample_profile_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                           double dxy, double inc, double dRA, double dDec, double PA, int64_t M,
+                           const double* u, const double* v, double* vis_out, void* stream) {
+  return sample_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, M, u, v,
+                                  vis_out, stream);
+}
+
+int gal_chi2_image_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                       double dDec, double PA, const gal_data* data, double* chi2_out,
+                       void* stream) {
+  return chi2_image_t<float>(ctx, image, nxy, dxy, dRA, dDec, PA, data, chi2_out, stream);
+}
+int gal_chi2_image_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                       double dDec, double PA, const gal_data* data, double* chi2_out,
+                       void* stream) {
+  return chi2_image_t<double>(ctx, image, nxy, dxy, dRA, dDec, PA, data, chi2_out, stream);
+}
+
+int gal_chi2_profile_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                         double dxy, double inc, double dRA, double dDec, double PA,
+                         const gal_data* data, double* chi2_out, void* stream) {
+  return chi2_profile_t<float>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
+                               chi2_out, stream);
+}
+int gal_chi2_profile_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                         double dxy, double inc, double dRA, double dDec, double PA,
+                         const gal_data* data, double* chi2_out, void* stream) {
+  return chi2_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
+                                chi2_out, stream);
+}
+
+int gal_chi2_image_host_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,
+                            double dRA, double dDec, double PA, const gal_data* data,
+                            double* chi2_host, void* stream) {
+  return chi2_image_host_t<float>(ctx, image_host, nxy, dxy, dRA, dDec, PA, data, chi2_host,
+                                  stream);
+}
+int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, double dxy,
+                            double dRA, double dDec, double PA, const gal_data* data,
+                            double* chi2_host, void* stream) {
+  return chi2_image_host_t<double>(ctx, image_host, nxy, dxy, dRA, dDec, PA, data, chi2_host,
+                                   stream);
+}
+
+}  // extern "C"

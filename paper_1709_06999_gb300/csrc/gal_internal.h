@@ -1,0 +1,44 @@
+// Internal interface between the C-ABI layer (gal_api.cu) and the kernel
+// translation units (gal_kernels_f32.cu, gal_kernels_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gal {
+
+// profile -> image parameters (all radians; Sect. 2 sampleProfile)
+struct SweepParams {
+  double Rmin, dR, dxy, inc;
+  int nr;
+};
+
+// per-call sampling parameters: cos/sin PA, S = nxy * dxy (grid cells per
+// wavelength^-1), and the phase offsets (dRA, dDec) so that the phase in turns
+// is u * phx + v * phy.
+struct GatherParams {
+  double cpa, spa, S, phx, phy;
+  int N;
+};
+
+// Host launchers, one explicit instantiation per precision.
+template <typename T> struct Launch {
+  static cudaError_t init();  // kernel attributes; once per process
+  static int gather_blocks_per_sm(bool chi2);
+  static cudaError_t twiddles(void* tw, int N, cudaStream_t st);
+  static cudaError_t extent(const T* u, const T* v, int64_t M, double* rho2, int blocks,
+                            cudaStream_t st);
+  static cudaError_t sweep(const T* I, const SweepParams& sp, int N, T* img, int blocks,
+                           cudaStream_t st);
+  static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
+                              const void* tw, void* F1, const double* rho2, double S,
+                              cudaStream_t st);
+  static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
+                              const double* rho2, double S, cudaStream_t st);
+  static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
+                            const T* u, const T* v, const T* re, const T* im, const T* w,
+                            int64_t M, void* vis, double* partials, unsigned* counter,
+                            double* chi2, int* err, int blocks, cudaStream_t st);
+};
+
+}  // namespace gal

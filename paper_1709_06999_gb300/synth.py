@@ -176,12 +176,18 @@ def ring_profile(nr: int, dR: float, Rmin: float, r0: float = 0.5 * ARCSEC,
     return np.exp(-(((r - r0) / width) ** 2)) * (r / ARCSEC) ** power
 
 
-def profile_problem(nxy: int = 1024, M: int = 1_000_000, nr: int = 8192, seed: int = 1) -> ProfileProblem:
+def profile_problem(nxy: int = 1024, M: int = 1_000_000, nr: int = 8192, seed: int = 1,
+                    dxy: float = 0.005 * ARCSEC) -> ProfileProblem:
     """chi2_profile case: Gaussian ring (r0=0.5", width 0.1") x r^-0.5, nr=8192,
     dR = 4.5"/8192, Rmin = dR/2, inclination 45 deg, nxy=1024, dxy=0.005",
-    uv as in the small image case with radius up to 0.45/dxy."""
-    dxy = 0.005 * ARCSEC
-    dR = 4.5 * ARCSEC / 8192
+    uv as in the small image case with radius up to 0.45/dxy.
+
+    Other (nxy, dxy, nr) scale the radial extent with the field of view
+    (4.5" for a 5.12" field covers the farthest pixel of the 45 deg image)
+    and keep the ring at the same place on the sky.
+    """
+    extent = 4.5 * ARCSEC * (nxy * dxy) / (5.12 * ARCSEC)
+    dR = extent / nr
     Rmin = dR / 2
     rng = np.random.default_rng(seed)
     I = ring_profile(nr, dR, Rmin)

@@ -1,0 +1,62 @@
+"""The C-ABI library loads and exports every symbol the header declares (CPU only)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "galario_gb300.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gal_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1709_06999_gb300 import _native
+    return _native.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for op in ("sweep", "sample_image", "sample_profile", "chi2_image", "chi2_profile"):
+        for p in ("f32", "f64"):
+            assert f"gal_{op}_{p}" in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(lib):
+    from paper_1709_06999_gb300 import _native
+    assert sorted(_native.EXPORTED) == _declared()
+
+
+def test_nm_lists_symbols_as_c(lib):
+    from paper_1709_06999_gb300 import _native
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (gal_\w+)", out))
+    assert set(_declared()) <= exported
+
+
+def test_status_strings(lib):
+    assert lib.gal_strerror(0) == b"ok"
+    assert lib.gal_strerror(-1) == b"invalid argument"
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import ctypes as ct
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ct.c_void_p()
+    assert lib.gal_create(ct.byref(h), 0) == -5
