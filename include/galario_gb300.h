@@ -164,6 +164,37 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
                             double dRA, double dDec, double PA, const gal_data* data,
                             double* chi2_host, void* stream);
 
+/* ---- allocation-free variant ---------------------------------------------------------- */
+
+/* Largest image side accepted by gal_chi2_image_noalloc_f32. */
+#define GAL_NOALLOC_MAX_NXY 1024
+
+/* chi2Image in float32 without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * -- for example a host application whose own allocator has already reserved
+ * the GPU's memory, a plug-in that may not grow the process's device
+ * footprint, or a latency-critical loop that cannot afford the device
+ * synchronisation an allocation implies.
+ *
+ * It computes what gal_data_create_f32 + gal_chi2_image_f32 compute (same
+ * kernels, same result) but takes the observation as plain arrays and needs no
+ * context.  Its scratch is one fixed device array of about 8.5 MB inside the
+ * library, present on every GPU that loads the library until the process
+ * exits; no call allocates or frees anything.
+ *   image     nxy*nxy floats (device), 8-byte aligned; nxy a power of two in
+ *             [4, GAL_NOALLOC_MAX_NXY] -- larger images return GAL_E_INVAL
+ *   u, v, re, im, w   M floats each (device), as for gal_data_create_f32
+ *   chi2_out  one double (device)
+ * The first call on a device (with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every call
+ * uses the same array and leaves its contents behind (each call re-initialises
+ * what it needs), so calls that may overlap on the GPU -- other streams, other
+ * host threads -- race with each other and must be serialised by the caller. */
+int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dxy, double dRA, double dDec,
+                               double PA, const float* u, const float* v, const float* re,
+                               const float* im, const float* w, int64_t M, double* chi2_out,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

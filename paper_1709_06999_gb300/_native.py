@@ -38,6 +38,8 @@ for _p in ("f32", "f64"):
         f"gal_chi2_image_host_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
     })
 
+_SIGNATURES["gal_chi2_image_noalloc_f32"] = (I32, [P, I32, D, D, D, D, P, P, P, P, P, I64, P, P])
+
 EXPORTED = sorted(_SIGNATURES)
 
 _lib = None
