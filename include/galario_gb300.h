@@ -89,7 +89,8 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4);
  * are borrowed (device memory, must outlive the handle).  Enqueues on `stream` one
  * reduction for the largest baseline sqrt(u^2+v^2) (Sect. 3.3, criterion (i)),
  * which later calls use to restrict the FFT to the part of the spectrum the uv
- * points can reach (an exact pruning). */
+ * points can reach (an exact pruning), and reads that one value back
+ * (synchronising `stream` once). */
 int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
                         const float* im, const float* w, int64_t M, void* stream, gal_data** out);
 int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
@@ -178,7 +179,7 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
  *
  * It computes what gal_data_create_f32 + gal_chi2_image_f32 compute (same
  * kernels, same result) but takes the observation as plain arrays and needs no
- * context.  Its scratch is one fixed device array of about 8.5 MB inside the
+ * context.  Its scratch is one fixed device array of about 12.7 MB inside the
  * library, present on every GPU that loads the library until the process
  * exits; no call allocates or frees anything.
  *   image     nxy*nxy floats (device), 8-byte aligned; nxy a power of two in

@@ -18,6 +18,10 @@ namespace {
 
 constexpr int kMaxLog2 = 13;  // nxy <= 8192
 constexpr int kStages = 4;    // 0 extent, 1 row pass, 2 column pass, 3 gather
+// largest spectrum window staged in shared memory by the chi2 gather: two
+// blocks per SM for float, one for double
+constexpr size_t kWindowSmemF32 = 100 * 1024;
+constexpr size_t kWindowSmemF64 = 200 * 1024;
 
 struct TimedStage {
   int stage;
@@ -31,7 +35,7 @@ struct gal_ctx {
   int num_sms = 0;
   void* F1 = nullptr;  // row-pass output (nxy x Kc complex)
   size_t F1_bytes = 0;
-  void* Gw = nullptr;  // pruned spectrum window (nrw x Kc complex)
+  void* Gw = nullptr;  // pruned spectrum window as node pairs (nrw x (Kc-1) x 2 complex)
   size_t Gw_bytes = 0;
   double* partials = nullptr;  // per-block chi2 partial sums
   int partials_len = 0;
@@ -42,7 +46,9 @@ struct gal_ctx {
   void* stage_img = nullptr;    // image staging for the host-buffer entry points
   size_t stage_img_bytes = 0;
   void* tw[2][kMaxLog2 + 1] = {};
-  int gather_blocks[2][2] = {};  // [f64?][chi2?]
+  int gather_blocks[2][2] = {};  // [f64?][chi2?], global-memory window
+  size_t smem_blocks_key[2] = {};  // window bytes the cached count below is for
+  int smem_blocks[2] = {};         // chi2 gather blocks with a shared-memory window
   int aux_blocks = 0;
   uint64_t launches = 0;
   bool timing = false;
@@ -59,12 +65,14 @@ struct gal_data {
   int64_t M = 0;
   const void *u = nullptr, *v = nullptr, *re = nullptr, *im = nullptr, *w = nullptr;
   double* rho2 = nullptr;  // device scalar: max(u^2 + v^2)
+  double rho2_host = 0.0;  // the same value, read back once at registration
 };
 
 namespace {
 
 int cuda_fail(gal_ctx* ctx, cudaError_t e) {
   if (ctx) snprintf(ctx->last_err, sizeof ctx->last_err, "%s", cudaGetErrorString(e));
+  (void)cudaGetLastError();  // a failed call must not poison the next launch check
   return e == cudaErrorMemoryAllocation ? GAL_E_NOMEM : GAL_E_CUDA;
 }
 
@@ -102,7 +110,7 @@ template <typename T> int ensure(gal_ctx* ctx, int nxy) {
   using C = gal::cplx_t<T>;
   const size_t spec = (size_t)nxy * (nxy / 2 + 1) * sizeof(C);
   GAL_CUDA(ctx, grow(&ctx->F1, &ctx->F1_bytes, spec));
-  GAL_CUDA(ctx, grow(&ctx->Gw, &ctx->Gw_bytes, spec));
+  GAL_CUDA(ctx, grow(&ctx->Gw, &ctx->Gw_bytes, 2 * spec));  // horizontal node pairs
   const int l = log2i(nxy);
   void*& tw = ctx->tw[prec_index<T>()][l];
   if (!tw) {
@@ -146,6 +154,9 @@ void harvest(gal_ctx* ctx, size_t keep) {
 // Launch wrapper: counts the launch and, when timing, brackets it with events.
 template <typename F> int stage(gal_ctx* ctx, int id, cudaStream_t st, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
+  // drop a launch error left behind by an earlier, unrelated runtime call so
+  // that the check after our launch reports our launch only
+  (void)cudaGetLastError();
   if (ctx->timing) {
     if (ctx->timed.size() > 8192) harvest(ctx, 4096);
     a = pool_event(ctx);
@@ -200,7 +211,7 @@ int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& s
   const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
   const double S = (double)nxy * dxy;
   GAL_TRY(stage(ctx, 1, st, [&] {
-    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, st);
+    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, st);
   }));
   GAL_TRY(stage(ctx, 2, st, [&] {
     return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, st);
@@ -227,7 +238,7 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   const int blocks = ctx->gather_blocks[prec_index<T>()][0];
   return stage(ctx, 3, st, [&] {
     return gal::Launch<T>::gather(ctx->Gw, gp, ctx->rho2, u, v, nullptr, nullptr, nullptr, M,
-                                  vis, nullptr, nullptr, nullptr, ctx->err, blocks, st);
+                                  vis, nullptr, nullptr, nullptr, 0, blocks, st);
   });
 }
 
@@ -245,12 +256,27 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
   }
   GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, st));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
-  const int blocks = ctx->gather_blocks[prec_index<T>()][1];
+  // Stage the kept spectrum window in shared memory when it is small enough
+  // (the pruned windows of long-baseline-free data usually are).
+  using C = gal::cplx_t<T>;
+  const gal::Bounds bd = gal::make_bounds(d->rho2_host, (double)nxy * dxy, nxy);
+  size_t wbytes = (size_t)bd.nrw * bd.Kc * sizeof(C);
+  if (wbytes > (sizeof(T) == 4 ? kWindowSmemF32 : kWindowSmemF64)) wbytes = 0;
+  int blocks = ctx->gather_blocks[prec_index<T>()][1];
+  if (wbytes) {
+    if (wbytes != ctx->smem_blocks_key[prec_index<T>()]) {
+      ctx->smem_blocks_key[prec_index<T>()] = wbytes;
+      ctx->smem_blocks[prec_index<T>()] =
+          ctx->num_sms * gal::Launch<T>::gather_blocks_per_sm(true, wbytes);
+    }
+    blocks = ctx->smem_blocks[prec_index<T>()];
+  }
+  if (blocks > ctx->partials_len) blocks = ctx->partials_len;
   return stage(ctx, 3, st, [&] {
     return gal::Launch<T>::gather(ctx->Gw, gp, d->rho2, static_cast<const T*>(d->u),
                                   static_cast<const T*>(d->v), static_cast<const T*>(d->re),
                                   static_cast<const T*>(d->im), static_cast<const T*>(d->w), d->M,
-                                  nullptr, ctx->partials, ctx->counter, chi2, ctx->err, blocks, st);
+                                  nullptr, ctx->partials, ctx->counter, chi2, wbytes, blocks, st);
   });
 }
 
@@ -335,6 +361,14 @@ int data_create_t(gal_ctx* ctx, const T* u, const T* v, const T* re, const T* im
   int s = stage(ctx, 0, st, [&] {
     return gal::Launch<T>::extent(u, v, M, d->rho2, ctx->aux_blocks, st);
   });
+  if (s == GAL_OK) {
+    // one read-back at registration: the host sizes the gather's shared
+    // window from it (the kernels read the device copy)
+    cudaError_t e2 = cudaMemcpyAsync(&d->rho2_host, d->rho2, sizeof(double),
+                                     cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) s = cuda_fail(ctx, e2);
+  }
   if (s != GAL_OK) {
     cudaFree(d->rho2);
     delete d;
@@ -398,10 +432,10 @@ int gal_create(gal_ctx** out, int device) {
   if (!ctx) return GAL_E_NOMEM;
   ctx->device = device;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  ctx->gather_blocks[0][0] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(false);
-  ctx->gather_blocks[0][1] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(true);
-  ctx->gather_blocks[1][0] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(false);
-  ctx->gather_blocks[1][1] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(true);
+  ctx->gather_blocks[0][0] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(false, 0);
+  ctx->gather_blocks[0][1] = ctx->num_sms * gal::Launch<float>::gather_blocks_per_sm(true, 0);
+  ctx->gather_blocks[1][0] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(false, 0);
+  ctx->gather_blocks[1][1] = ctx->num_sms * gal::Launch<double>::gather_blocks_per_sm(true, 0);
   ctx->aux_blocks = ctx->num_sms * 8;
   int maxb = 0;
   for (auto& a : ctx->gather_blocks)

@@ -129,4 +129,14 @@ __host__ __device__ __forceinline__ Bounds make_bounds(double rho2, double S, in
   return b;
 }
 
+// Bounds for the whole block: one thread evaluates them (FP64: GB300's FP64
+// pipe is narrow, so no per-thread FP64 work) and shares them.  Every thread
+// of the block must call it.
+__device__ __forceinline__ Bounds block_bounds(const double* rho2, double S, int N) {
+  __shared__ Bounds sb;
+  if (threadIdx.x == 0) sb = make_bounds(*rho2, S, N);
+  __syncthreads();
+  return sb;
+}
+
 }  // namespace gal

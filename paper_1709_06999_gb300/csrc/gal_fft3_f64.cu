@@ -1,0 +1,9 @@
+// Compile-time-length FFT passes, float64 instantiations.
+#include "gal_fft3_launch.cuh"
+namespace gal {
+template cudaError_t row_fft3<double>(const double*, const double*, const SweepParams&, int,
+                                      const void*, void*, const double*, double, int*,
+                                      cudaStream_t);
+template cudaError_t col_fft3<double>(const void*, void*, int, const void*, const double*, double,
+                                      cudaStream_t);
+}  // namespace gal

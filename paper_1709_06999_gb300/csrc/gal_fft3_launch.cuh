@@ -1,0 +1,120 @@
+// Launchers of the compile-time-length row and column passes: one kernel
+// instantiation per transform length, chosen by a switch on log2 of it.
+#pragma once
+
+#include "gal_kernels.cuh"
+
+namespace gal {
+
+// set a kernel's dynamic shared-memory limit once per process (one flag per
+// kernel: the template argument is the kernel itself)
+template <auto Kern> cudaError_t ensure_smem_attr(size_t smem) {
+  static size_t done = 0;
+  if (smem <= 48 * 1024 || done >= smem) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+  if (e == cudaSuccess) done = smem;
+  return e;
+}
+
+template <typename T, int LG, bool SWEEP>
+cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const void* tw,
+                        void* F1, const double* rho2, double S, int* err, cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int M = 1 << LG, N = 2 * M;
+  using SH = Shape3<T, M, N>;
+  const C* twc = static_cast<const C*>(tw);
+  C* out = static_cast<C*>(F1);
+  if constexpr (!SWEEP) {
+    constexpr auto kern = row_fft3_kernel<T, LG, true, false>;
+    const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
+    cudaError_t e = ensure_smem_attr<kern>(smem);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+    if (e) return e;
+    if (per_sm < 1) per_sm = 1;
+    int grid = per_sm * current_device_sms();
+    if (grid > N / SH::G) grid = N / SH::G;
+    kern<<<grid, SH::threads, smem, st>>>(image, nullptr, SweepT<T>{}, twc, out, rho2, S, err);
+  } else {
+    constexpr auto kern = row_fft3_kernel<T, LG, false, true>;
+    const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
+    const cudaError_t e = ensure_smem_attr<kern>(smem);
+    if (e) return e;
+    kern<<<N / SH::G, SH::threads, smem, st>>>(nullptr, I, sweep_cast<T>(sp), twc, out, rho2, S,
+                                               err);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int LG>
+cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
+                        cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int N = 1 << LG;
+  using SH = Shape3<T, N, (1 << 30)>;
+  constexpr auto kern = col_fft3_kernel<T, LG>;
+  const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
+  const cudaError_t e = ensure_smem_attr<kern>(smem);
+  if (e) return e;
+  const int P = N / 2 + 1;
+  int grid = (P + SH::G - 1) / SH::G;
+  const int cap = 2 * current_device_sms();
+  if (grid > cap) grid = cap;
+  kern<<<grid, SH::threads, smem, st>>>(static_cast<const C*>(F1), static_cast<C*>(Gw),
+                                        static_cast<const C*>(tw), rho2, S);
+  return cudaGetLastError();
+}
+
+template <typename T, int LG>
+cudaError_t row3_switch(int lg, const T* image, const T* I, const SweepParams& sp,
+                        const void* tw, void* F1, const double* rho2, double S, int* err,
+                        cudaStream_t st) {
+  if constexpr (LG > 12) {
+    return cudaErrorNotSupported;
+  } else {
+    if (lg == LG) {
+      if (I) return launch_row3<T, LG, true>(image, I, sp, tw, F1, rho2, S, err, st);
+      return launch_row3<T, LG, false>(image, I, sp, tw, F1, rho2, S, err, st);
+    }
+    return row3_switch<T, LG + 1>(lg, image, I, sp, tw, F1, rho2, S, err, st);
+  }
+}
+
+// largest column length with both ping-pong buffers in shared memory:
+// 8192 float2 (2 x 8704 x 8 B) but 4096 double2 (8192 would need 295 KB)
+template <typename T> constexpr int col3_max_lg() { return sizeof(T) == 4 ? 13 : 12; }
+
+template <typename T, int LG>
+cudaError_t col3_switch(int lg, const void* F1, void* Gw, const void* tw, const double* rho2,
+                        double S, cudaStream_t st) {
+  if constexpr (LG > col3_max_lg<T>()) {
+    return cudaErrorNotSupported;
+  } else {
+    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, st);
+    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, st);
+  }
+}
+
+inline int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename T>
+cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
+                     void* F1, const double* rho2, double S, int* err, cudaStream_t st) {
+  constexpr int LG0 = ilog2c(FftV<T>::V);
+  return row3_switch<T, LG0>(ilog2i(N / 2), image, I, sp, tw, F1, rho2, S, err, st);
+}
+
+template <typename T>
+cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
+                     cudaStream_t st) {
+  constexpr int LG0 = ilog2c(FftV<T>::V);
+  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, st);
+}
+
+}  // namespace gal

@@ -24,21 +24,34 @@ struct GatherParams {
 // Host launchers, one explicit instantiation per precision.
 template <typename T> struct Launch {
   static cudaError_t init();  // kernel attributes; once per process
-  static int gather_blocks_per_sm(bool chi2);
+  // resident gather blocks per SM; window_smem > 0 selects the variant that
+  // stages the spectrum window (that many bytes) in shared memory
+  static int gather_blocks_per_sm(bool chi2, size_t window_smem);
   static cudaError_t twiddles(void* tw, int N, cudaStream_t st);
   static cudaError_t extent(const T* u, const T* v, int64_t M, double* rho2, int blocks,
                             cudaStream_t st);
   static cudaError_t sweep(const T* I, const SweepParams& sp, int N, T* img, int blocks,
                            cudaStream_t st);
+  // err: bit 2 is set if a staged copy's wait timed out (never expected)
   static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
-                              const void* tw, void* F1, const double* rho2, double S,
+                              const void* tw, void* F1, const double* rho2, double S, int* err,
                               cudaStream_t st);
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
                               const double* rho2, double S, cudaStream_t st);
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
                             int64_t M, void* vis, double* partials, unsigned* counter,
-                            double* chi2, int* err, int blocks, cudaStream_t st);
+                            double* chi2, size_t window_smem, int blocks, cudaStream_t st);
 };
+
+// Compile-time-length FFT passes (gal_fft3.cuh), instantiated per precision in
+// gal_fft3_f32.cu / gal_fft3_f64.cu.  They return cudaErrorNotSupported when
+// the length is outside their range (the caller then uses the generic passes).
+template <typename T>
+cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
+                     void* F1, const double* rho2, double S, int* err, cudaStream_t st);
+template <typename T>
+cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
+                     cudaStream_t st);
 
 }  // namespace gal

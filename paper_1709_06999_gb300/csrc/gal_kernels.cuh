@@ -13,6 +13,9 @@
 
 #include "gal_common.cuh"
 #include "gal_fft.cuh"
+#include "gal_fft2.cuh"
+#include "gal_fft3.cuh"
+#include "gal_tma.cuh"
 #include "gal_internal.h"
 
 namespace gal {
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
   const int row = blockIdx.x * rpb + g;
   const bool active = row < N;
   C* s = sm + (size_t)g * M;
-  const Bounds bd = make_bounds(*rho2, S, N);
+  const Bounds bd = block_bounds(rho2, S, N);
 
   if (active) {
     const int irow = (row + M) & (N - 1);
@@ -188,35 +191,265 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
 // ---------------------------------------------------------------------------
 // Column pass.  For each kept column c < Kc: complex FFT over the N rows of
 // F1 (pitch Kc), then the v-axis fftshift: output row r holds frequency
-// kv = (r + N/2) mod N.  Only rows r0 .. r0+nrw-1 are written, to the window
-// Gw (nrw x Kc, pitch Kc).
+// kv = (r + N/2) mod N.  Only rows r0 .. r0+nrw-1 are kept, written to the
+// window Gp[rr Kc + c] (nrw x Kc).  Blocks loop over column groups (grid capped at a few blocks per SM), so a
+// heavily pruned spectrum launches no idle blocks.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(1024) col_pass_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gw, int N,
-                                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2,
-                                double S) {
+__global__ void __launch_bounds__(1024)
+col_pass_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gp, int N,
+                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S) {
   using C = cplx_t<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  const Bounds bd = make_bounds(*rho2, S, N);
+  const Bounds bd = block_bounds(rho2, S, N);
   const int Tg = N >= 8 ? N / 8 : 1;
   const int cpb = blockDim.x / Tg;
-  const int c0 = blockIdx.x * cpb;
-  if (c0 >= bd.Kc) return;  // uniform over the block
   const int g = threadIdx.x / Tg, t = threadIdx.x % Tg;
   const int ld = N + 1;  // padded column stride in shared memory
-  for (int q = threadIdx.x; q < cpb * N; q += blockDim.x) {
-    const int cl = q % cpb, i = q / cpb, c = c0 + cl;
-    sm[(size_t)cl * ld + i] = c < bd.Kc ? F1[(size_t)i * bd.Kc + c] : mkc((T)0, (T)0);
-  }
-  __syncthreads();
-  fft_inplace(sm + (size_t)g * ld, N, t, Tg, tw, 1);
-  for (int q = threadIdx.x; q < cpb * bd.nrw; q += blockDim.x) {
-    const int cl = q % cpb, rr = q / cpb, c = c0 + cl;
-    if (c < bd.Kc) {
-      const int kv = (bd.r0 + rr + N / 2) & (N - 1);
-      Gw[(size_t)rr * bd.Kc + c] = sm[(size_t)cl * ld + kv];
+  for (int c0 = blockIdx.x * cpb; c0 < bd.Kc; c0 += gridDim.x * cpb) {
+    for (int q = threadIdx.x; q < cpb * N; q += blockDim.x) {
+      const int cl = q % cpb, i = q / cpb, c = c0 + cl;
+      sm[(size_t)cl * ld + i] = c < bd.Kc ? F1[(size_t)i * bd.Kc + c] : mkc((T)0, (T)0);
     }
+    __syncthreads();
+    fft_inplace(sm + (size_t)g * ld, N, t, Tg, tw, 1);
+    for (int q = threadIdx.x; q < cpb * bd.nrw; q += blockDim.x) {
+      const int cl = q % cpb, rr = q / cpb, c = c0 + cl;
+      if (c < bd.Kc) {
+        const int kv = (bd.r0 + rr + N / 2) & (N - 1);
+        const C val = sm[(size_t)cl * ld + kv];
+        Gp[(size_t)rr * bd.Kc + c] = val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Compile-time-length row and column passes (gal_fft3.cuh), used whenever the
+// transform length is at least V.
+// ---------------------------------------------------------------------------
+template <typename T> struct FftV;
+template <> struct FftV<float> { static constexpr int V = 16; };
+template <> struct FftV<double> { static constexpr int V = 8; };
+
+// X_k = (A + B)/2 - (i/2) W (A - B), A = Z_k, B = conj Z_{M-k}, W = W_N^k
+template <typename C> __device__ __forceinline__ C r2c_unpack(C zk, C zmk, C w) {
+  using R = decltype(zk.x);
+  const C b = cconj(zmk);
+  const C e = mkc((R)0.5 * (zk.x + b.x), (R)0.5 * (zk.y + b.y));
+  const C d = mkc((R)0.5 * (zk.x - b.x), (R)0.5 * (zk.y - b.y));
+  return cadd(e, cmul(cmul_mi(d), w));
+}
+
+// Launch shape of the length-L passes: G sequences per block (at least 128
+// threads), each with a shared-memory region of RS complex (padded, rounded
+// to 16 bytes so that bulk copies into it stay aligned).
+template <typename T, int L, int NSEQ> struct Shape3 {
+  using C = cplx_t<T>;
+  static constexpr int V = FftV<T>::V;
+  using P = P3<L, V>;
+  static constexpr int G0 = P::T >= 128 ? 1 : 128 / P::T;
+  static constexpr int G = G0 < NSEQ ? G0 : NSEQ;
+  static constexpr int threads = G * P::T;
+  static constexpr int RS = (P::padded * (int)sizeof(C) + 15) / 16 * 16 / (int)sizeof(C);
+};
+
+// Row pass: row i' of F1 (pitch Kc) = first Kc bins of the real-to-complex FFT
+// of row i' of fftshift(image), i.e. of image row (i' + N/2) mod N with its
+// halves swapped, read as z_n = x_{2n} + i x_{2n+1} (M = N/2 points).
+// TMA: persistent blocks own row groups blockIdx.x + k gridDim.x; thread 0
+// keeps the next group in flight with bulk copies (the two half-row copies
+// perform the fftshift) into a two-slot ring completed on one mbarrier per
+// slot; each group is transformed in place (its slot and one work buffer).
+// A wait that times out (never expected) sets bit 2 of *err, drains the
+// copies still in flight (bounded) and ends the block.
+// Otherwise (SWEEP, or an image that is not 16-byte aligned) each block loads
+// or generates its rows directly.
+template <typename T, int LG, bool TMA, bool SWEEP>
+__global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads)
+row_fft3_kernel(const T* __restrict__ image, const T* __restrict__ I, SweepT<T> sp,
+                const cplx_t<T>* __restrict__ tw, cplx_t<T>* __restrict__ F1,
+                const double* __restrict__ rho2, double S, int* __restrict__ err) {
+  using C = cplx_t<T>;
+  constexpr int M = 1 << LG, N = 2 * M;
+  using SH = Shape3<T, M, N>;
+  using P = typename SH::P;
+  constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  C* base = reinterpret_cast<C*>(smem_raw + 128);
+  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
+  const Bounds bd = block_bounds(rho2, S, N);
+  C tw1[V - 1];
+  load_tw1<M, V, 2>(tw1, t, tw);
+  const bool pruned = P::nstage >= 2 && bd.Kc <= P::Nsl;
+  const bool one_j = bd.Kc <= TT;
+  C twp[V];
+  C wj = mkc((T)0, (T)0);
+  if (pruned && one_j && t < bd.Kc) {
+    load_twp<M, V, 2>(twp, t, tw);
+    wj = __ldg(tw + t);
+  }
+  auto sync = [] { __syncthreads(); };
+  // Transform the group held in registers v (stage-0 layout), A, B: buffers.
+  auto transform = [&](C (&v)[V], C* A, C* B, int row) {
+    Head3<M, V, 2, 0>::run(v, A, B, t, tw, tw1, sync);
+    C* in = last_input<M, V>(A, B);
+    C* out = F1 + (size_t)row * bd.Kc;
+    if (pruned) {
+      for (int j = t; j < bd.Kc; j += TT) {
+        C zj, zmj;
+        if (one_j) {
+          pruned_pair3<M, V>(in, j, twp, zj, zmj);
+          out[j] = r2c_unpack(zj, zmj, wj);
+        } else {
+          C tj[V];
+          load_twp<M, V, 2>(tj, j, tw);
+          pruned_pair3<M, V>(in, j, tj, zj, zmj);
+          out[j] = r2c_unpack(zj, zmj, __ldg(tw + j));
+        }
+      }
+    } else {
+      last_full<M, V, 2>(v, in, t, tw);
+      C* o = in == A ? B : A;
+      store_full<M, V>(v, o, t);
+      __syncthreads();
+      for (int k = t; k < bd.Kc; k += TT)
+        out[k] = r2c_unpack(o[pad3<V>(k & (M - 1))], o[pad3<V>((M - k) & (M - 1))], __ldg(tw + k));
+    }
+  };
+  if constexpr (TMA) {
+    C* slot0 = base;
+    C* work = base + 2 * G * RS;
+    const int ngroups = N / G;
+    const uint32_t half_bytes = (uint32_t)(M * sizeof(T));
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int it) {  // thread 0 only
+      const int grp = blockIdx.x + it * gridDim.x;
+      if (grp >= ngroups) return;
+      const int sl = it & 1;
+      mbar_arrive_expect_tx(&bars[sl], 2u * half_bytes * (uint32_t)G);
+      for (int rl = 0; rl < G; ++rl) {
+        const T* src = image + (size_t)(((grp * G + rl) + M) & (N - 1)) * N;
+        T* dst = reinterpret_cast<T*>(slot0 + (size_t)(sl * G + rl) * RS);
+        bulk_load(dst, src + M, half_bytes, &bars[sl]);
+        bulk_load(dst + M, src, half_bytes, &bars[sl]);
+      }
+    };
+    if (threadIdx.x == 0) {
+      issue(0);
+      issue(1);
+    }
+    for (int it = 0;; ++it) {
+      const int grp = blockIdx.x + it * gridDim.x;
+      if (grp >= ngroups) break;
+      const int sl = it & 1;
+      const bool ok = mbar_wait(&bars[sl], (uint32_t)((it >> 1) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+          atomicOr(err, 2);
+          for (int k = it; k < it + 2; ++k)
+            if (blockIdx.x + k * gridDim.x < ngroups) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1));
+        }
+        return;
+      }
+      C* slot = slot0 + (size_t)(sl * G + g) * RS;
+      C v[V];
+#pragma unroll
+      for (int r = 0; r < V; ++r) v[r] = slot[t + r * TT];
+      // stage 0 writes the work buffer; the slot is reused from stage 1 on,
+      // after the barrier that ends stage 0
+      transform(v, work + (size_t)g * RS, slot, grp * G + g);
+      __syncthreads();  // every read of this slot is done
+      if (threadIdx.x == 0) issue(it + 2);
+    }
+  } else {
+    C* A = base + (size_t)g * RS;
+    C* B = base + (size_t)(G + g) * RS;
+    const int row = blockIdx.x * G + g;
+    const int irow = (row + M) & (N - 1);
+    C v[V];
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+      const int n = t + r * TT;
+      const int j = (2 * n + M) & (N - 1);
+      if constexpr (SWEEP)
+        v[r] = mkc(sweep_pixel(I, sp, N, irow, j), sweep_pixel(I, sp, N, irow, j + 1));
+      else
+        v[r] = *reinterpret_cast<const C*>(image + (size_t)irow * N + j);
+    }
+    transform(v, A, B, row);
+  }
+}
+
+// Column pass: for each kept column c < Kc (blocks loop over column groups),
+// the complex FFT of length N down column c of F1 (pitch Kc); output row r
+// of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
+// r0 + nrw - 1 are written to the window Gw (nrw x Kc).  When the window is
+// pruned, only the kept frequencies +-j are evaluated.
+template <typename T, int LG>
+__global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads)
+col_fft3_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gw,
+                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S) {
+  using C = cplx_t<T>;
+  constexpr int N = 1 << LG;
+  using SH = Shape3<T, N, (1 << 30)>;
+  using P = typename SH::P;
+  constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* base = reinterpret_cast<C*>(smem_raw);
+  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
+  const Bounds bd = block_bounds(rho2, S, N);
+  C tw1[V - 1];
+  load_tw1<N, V, 1>(tw1, t, tw);
+  const int kmax = N / 2 - bd.r0;
+  const bool pruned = P::nstage >= 2 && bd.r0 > 0 && kmax < P::Nsl;
+  const bool one_j = kmax < TT;
+  C twp[V];
+  if (pruned && one_j && t <= kmax) load_twp<N, V, 1>(twp, t, tw);
+  C* A = base + (size_t)g * RS;
+  C* B = base + (size_t)(G + g) * RS;
+  auto sync = [] { __syncthreads(); };
+  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += gridDim.x * G) {
+    const int c = c0 + g;
+    const bool act = c < bd.Kc;
+    C v[V];
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = act ? F1[(size_t)(t + r * TT) * bd.Kc + c] : mkc((T)0, (T)0);
+    Head3<N, V, 1, 0>::run(v, A, B, t, tw, tw1, sync);
+    C* in = last_input<N, V>(A, B);
+    if (pruned) {
+      for (int j = t; j <= kmax; j += TT) {
+        C xj, xmj;
+        if (one_j) {
+          pruned_pair3<N, V>(in, j, twp, xj, xmj);
+        } else {
+          C tj[V];
+          load_twp<N, V, 1>(tj, j, tw);
+          pruned_pair3<N, V>(in, j, tj, xj, xmj);
+        }
+        if (act) {
+          Gw[(size_t)(kmax + j) * bd.Kc + c] = xj;
+          if (j > 0) Gw[(size_t)(kmax - j) * bd.Kc + c] = xmj;
+        }
+      }
+    } else {
+      last_full<N, V, 1>(v, in, t, tw);
+      C* o = in == A ? B : A;
+      store_full<N, V>(v, o, t);
+      __syncthreads();
+      if (act)
+        for (int rr = t; rr < bd.nrw; rr += TT)
+          Gw[(size_t)rr * bd.Kc + c] = o[pad3<V>((bd.r0 + rr + N / 2) & (N - 1))];
+    }
+    __syncthreads();
   }
 }
 
@@ -226,126 +459,172 @@ __global__ void __launch_bounds__(1024) col_pass_kernel(const cplx_t<T>* __restr
 // phase factor exp(+2 pi i (u dRA + v dDec)) (Sect. 3.2, App. D sign; the
 // offset rotates with the uv points, and the dot product is rotation
 // invariant, so the unrotated u, v are used).
+//
+// Clamping is done against the kept window.  When the window is pruned no
+// point can reach its edge, and when it is not pruned it is the whole half
+// spectrum, so window clamping is exactly the node-range clamping of App. D.
 // ---------------------------------------------------------------------------
-
-// position x = xh + xl clamped to [0, n-1]; cell c in [0, n-2], fraction f
-__device__ __forceinline__ void cell_ff(float xh, float xl, int n, int& c, float& f) {
-  float fl = floorf(xh);
-  float fr = (xh - fl) + xl;
-  if (fr < 0.f) {
-    fl -= 1.f;
-    fr += 1.f;
-  } else if (fr >= 1.f) {
-    fl += 1.f;
-    fr -= 1.f;
-  }
-  if (fl < 0.f) {
-    c = 0;
-    f = 0.f;
-  } else if (fl >= (float)(n - 1)) {
-    c = n - 2;
-    f = 1.f;
-  } else {
-    c = (int)fl;
-    f = fr;
-  }
-}
-
-__device__ __forceinline__ void cell_d(double x, int n, int& c, double& f) {
-  x = fmin(fmax(x, 0.0), (double)(n - 1));
-  double fl = floor(x);
-  if (fl > (double)(n - 2)) fl = (double)(n - 2);
-  c = (int)fl;
-  f = x - fl;
+struct Window {
+  int pitch;  // Kc nodes per row
+  int cmax;   // last cell column, Kc - 2
+  int rmax;   // last cell row, nrw - 2
+  int rofs;   // N/2 - r0: window row of v = 0
+};
+__device__ __forceinline__ Window make_window(const Bounds& b, int N) {
+  Window w;
+  w.pitch = b.Kc;
+  w.cmax = b.Kc - 2;
+  w.rmax = b.nrw - 2;
+  w.rofs = N / 2 - b.r0;
+  return w;
 }
 
 template <typename T> struct GatherT;
 
+// float path: A = cos(PA) N dxy and B = sin(PA) N dxy turn (u, v) into grid
+// offsets x = u A - v B (along u') and y = u B + v A (along v'); PX, PY are
+// dRA and dDec (turns per wavelength).  All four are float-float.
 template <> struct GatherT<float> {
-  ff cpa, spa, S, phx, phy;
-  float half;
+  ff A, B, PX, PY;
   double Sd;
-  int N, P;
+  int N;
   __host__ static GatherT make(const GatherParams& g) {
     GatherT r;
+    r.A = ff_split(g.cpa * g.S);
+    r.B = ff_split(g.spa * g.S);
+    r.PX = ff_split(g.phx);
+    r.PY = ff_split(g.phy);
     r.Sd = g.S;
-    r.cpa = ff_split(g.cpa);
-    r.spa = ff_split(g.spa);
-    r.S = ff_split(g.S);
-    r.phx = ff_split(g.phx);
-    r.phy = ff_split(g.phy);
-    r.half = (float)(g.N / 2);
     r.N = g.N;
-    r.P = g.N / 2 + 1;
     return r;
   }
 };
 
 template <> struct GatherT<double> {
-  double cpa, spa, S, phx, phy, half;
+  double cpa, spa, S, phx, phy;
   double Sd;
-  int N, P;
+  int N;
   __host__ static GatherT make(const GatherParams& g) {
     GatherT r;
-    r.Sd = g.S;
     r.cpa = g.cpa;
     r.spa = g.spa;
     r.S = g.S;
     r.phx = g.phx;
     r.phy = g.phy;
-    r.half = (double)(g.N / 2);
+    r.Sd = g.S;
     r.N = g.N;
-    r.P = g.N / 2 + 1;
     return r;
   }
 };
 
-template <typename C>
-__device__ __forceinline__ C window_bilinear(const C* __restrict__ Gw, const Bounds& bd, int r, int c,
-                                             decltype(C().x) fr, decltype(C().x) fc,
-                                             int* __restrict__ err) {
-  int rr = r - bd.r0;
-  if (rr < 0 || rr + 1 >= bd.nrw || c + 1 >= bd.Kc) {  // never taken: the window is exact
-    atomicOr(err, 1);
-    rr = min(max(rr, 0), bd.nrw - 2);
-    c = min(c, bd.Kc - 2);
-  }
-  const C* g = Gw + (size_t)rr * bd.Kc + c;
-  const C g00 = __ldg(g), g01 = __ldg(g + 1);
-  const C g10 = __ldg(g + bd.Kc), g11 = __ldg(g + bd.Kc + 1);
-  return clerp(clerp(g00, g01, fc), clerp(g10, g11, fc), fr);
+// a * b exactly as hi + lo (b float-float): hi = a b.hi rounded, lo = the rest
+__device__ __forceinline__ float prod_hi_lo(float a, ff b, float& lo) {
+  const float hi = a * b.hi;
+  lo = fmaf(a, b.lo, fmaf(a, b.hi, -hi));
+  return hi;
 }
 
-__device__ __forceinline__ float2 sample_point(const float2* __restrict__ Gw, const Bounds& bd,
-                                               const GatherT<float>& p, float u, float v,
-                                               int* __restrict__ err) {
+// cell and fraction of a position given as hi + lo; the cell is floor(pos),
+// the fraction pos - cell in [0, 1)
+__device__ __forceinline__ void split_cell(float h, float l, float& cell, float& frac) {
+  cell = floorf(h);
+  frac = (h - cell) + l;
+  if (frac < 0.f) {
+    cell -= 1.f;
+    frac += 1.f;
+  } else if (frac >= 1.f) {
+    cell += 1.f;
+    frac -= 1.f;
+  }
+  cell = fminf(fmaxf(cell, -32768.f), 32768.f);
+}
+
+// a window node from global memory (read-only cache) or from shared memory
+template <bool SMEM, typename C> __device__ __forceinline__ C ld_node(const C* p) {
+  if constexpr (SMEM) return *p;
+  else return __ldg(p);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__ Gp, const Window& w,
+                                               const GatherT<float>& p, float u, float v) {
   if (!(isfinite(u) && isfinite(v))) return make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
-  ff up = ff_add(ff_mul_f(u, p.cpa), ff_neg(ff_mul_f(v, p.spa)));
-  ff vp = ff_add(ff_mul_f(u, p.spa), ff_mul_f(v, p.cpa));
-  const bool neg = up.hi < 0.f;
+  float xae, xbe, yae, ybe;
+  const float xa = prod_hi_lo(u, p.A, xae), xb = prod_hi_lo(v, p.B, xbe);
+  const float ya = prod_hi_lo(u, p.B, yae), yb = prod_hi_lo(v, p.A, ybe);
+  // x = (xa - xb) + errors, y = (ya + yb) + errors, each as hi + lo (TwoSum)
+  float xh = xa - xb;
+  float t = xh - xa;
+  float xl = ((xa - (xh - t)) - (xb + t)) + (xae - xbe);
+  float yh = ya + yb;
+  t = yh - ya;
+  float yl = ((ya - (yh - t)) + (yb - t)) + (yae + ybe);
+  const bool neg = xh < 0.f;  // Hermitian fold: use (-u', -v') and conjugate
   if (neg) {
-    up = ff_neg(up);
-    vp = ff_neg(vp);
+    xh = -xh;
+    xl = -xl;
+    yh = -yh;
+    yl = -yl;
   }
-  const ff iu = ff_mul(up, p.S);
-  const ff iv = ff_add_f(ff_mul(vp, p.S), p.half);
-  int r, c;
-  float fr, fc;
-  cell_ff(iv.hi, iv.lo, p.N, r, fr);
-  cell_ff(iu.hi, iu.lo, p.P, c, fc);
-  float2 V = window_bilinear(Gw, bd, r, c, fr, fc, err);
-  if (neg) V.y = -V.y;
-  const ff ph = ff_add(ff_mul_f(u, p.phx), ff_mul_f(v, p.phy));
-  const float n = rintf(ph.hi);
-  const float fph = (ph.hi - n) + ph.lo;
+  float cf, fu, rf, fv;
+  split_cell(xh, xl, cf, fu);
+  split_cell(yh, yl, rf, fv);
+  int c = (int)cf;
+  if (c < 0) {
+    c = 0;
+    fu = 0.f;
+  } else if (c > w.cmax) {
+    c = w.cmax;
+    fu = 1.f;
+  }
+  int r = (int)rf + w.rofs;
+  if (r < 0) {
+    r = 0;
+    fv = 0.f;
+  } else if (r > w.rmax) {
+    r = w.rmax;
+    fv = 1.f;
+  }
+  const float2* g = Gp + (size_t)r * w.pitch + c;
+  const float2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
+  const float2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
+  const float ar = fmaf(fu, g01.x - g00.x, g00.x), ai = fmaf(fu, g01.y - g00.y, g00.y);
+  const float br = fmaf(fu, g11.x - g10.x, g10.x), bi = fmaf(fu, g11.y - g10.y, g10.y);
+  const float Vr = fmaf(fv, br - ar, ar);
+  float Vi = fmaf(fv, bi - ai, ai);
+  if (neg) Vi = -Vi;
+  // phase in turns, reduced exactly: each product hi is reduced by its own
+  // nearest integer before the sum, then the low parts are added
+  float pae, pbe;
+  const float pa = prod_hi_lo(u, p.PX, pae), pb = prod_hi_lo(v, p.PY, pbe);
+  float f = (pa - rintf(pa)) + (pb - rintf(pb));
+  f += pae + pbe;
+  f -= rintf(f);
   float sn, cs;
-  sincospif(2.f * fph, &sn, &cs);
-  return cmul(V, make_float2(cs, sn));
+  __sincosf(6.28318530717958647692f * f, &sn, &cs);  // |arg| <= pi
+  return make_float2(Vr * cs - Vi * sn, Vr * sn + Vi * cs);
 }
 
-__device__ __forceinline__ double2 sample_point(const double2* __restrict__ Gw, const Bounds& bd,
-                                                const GatherT<double>& p, double u, double v,
-                                                int* __restrict__ err) {
+// cell of the position ofs + x (x relative to the window's origin row or
+// column ofs), clamped to the window's node range [0, last + 1].  The floor
+// is taken of x itself so the result does not depend on the window's size.
+__device__ __forceinline__ void cell_d(double x, int ofs, int last, int& c, double& f) {
+  double fl = floor(x);
+  f = x - fl;
+  fl = fmin(fmax(fl, -1.0e9), 1.0e9);
+  c = (int)fl + ofs;
+  if (c < 0) {
+    c = 0;
+    f = 0.0;
+  } else if (c > last) {
+    c = last;
+    f = 1.0;
+  }
+}
+
+template <bool SMEM>
+__device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict__ Gp, const Window& w,
+                                                const GatherT<double>& p, double u, double v) {
   if (!(isfinite(u) && isfinite(v)))
     return make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
   double up = u * p.cpa - v * p.spa;
@@ -357,9 +636,12 @@ __device__ __forceinline__ double2 sample_point(const double2* __restrict__ Gw, 
   }
   int r, c;
   double fr, fc;
-  cell_d(p.half + vp * p.S, p.N, r, fr);
-  cell_d(up * p.S, p.P, c, fc);
-  double2 V = window_bilinear(Gw, bd, r, c, fr, fc, err);
+  cell_d(vp * p.S, w.rofs, w.rmax, r, fr);
+  cell_d(up * p.S, 0, w.cmax, c, fc);
+  const double2* g = Gp + (size_t)r * w.pitch + c;
+  const double2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
+  const double2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
+  double2 V = clerp(clerp(g00, g01, fc), clerp(g10, g11, fc), fr);
   if (neg) V.y = -V.y;
   const double ph = u * p.phx + v * p.phy;
   const double fph = ph - rint(ph);
@@ -369,10 +651,42 @@ __device__ __forceinline__ double2 sample_point(const double2* __restrict__ Gw, 
 }
 
 // per-thread compensated accumulators
-struct AccF {  // float-float running sum
-  ff s{0.f, 0.f};
-  __device__ __forceinline__ void add(float x) { s = ff_add_f(s, x); }
-  __device__ __forceinline__ double value() const { return (double)s.hi + (double)s.lo; }
+// block-wide sum of one double per thread, fixed order; result valid in thread 0
+__device__ __forceinline__ double block_sum(double x, double* ws);
+
+struct AccF {  // Kahan: s holds the sum, c the negated lost low-order part
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  // Block total (valid in thread 0): float-float tree inside each warp, FP64
+  // across warps, so that no per-thread FP64 arithmetic is issued.
+  __device__ __forceinline__ double block_total(double* ws) const {
+    ff a;
+    a.hi = s;
+    a.lo = -c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ff b;
+      b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+      b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+      a = ff_add(a, b);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) ws[warp] = (double)a.hi + (double)a.lo;
+    __syncthreads();
+    double x = 0.0;
+    if (warp == 0) {
+      x = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    }
+    return x;
+  }
 };
 struct AccD {  // Neumaier
   double s = 0.0, c = 0.0;
@@ -382,6 +696,7 @@ struct AccD {  // Neumaier
     s = t;
   }
   __device__ __forceinline__ double value() const { return s + c; }
+  __device__ __forceinline__ double block_total(double* ws) const { return block_sum(value(), ws); }
 };
 template <typename T> struct Acc;
 template <> struct Acc<float> { using type = AccF; };
@@ -402,7 +717,6 @@ __device__ __forceinline__ void load16(const T* __restrict__ p, int64_t q, T (&o
   }
 }
 
-// block-wide sum of one double per thread, fixed order; result valid in thread 0
 __device__ __forceinline__ double block_sum(double x, double* ws) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -419,17 +733,35 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
   return x;
 }
 
-template <typename T, bool CHI2>
-__global__ void __launch_bounds__(256)
+// SMEM: the block first copies the kept window (nrw x Kc nodes) into shared
+// memory and gathers from there; the random 4-node reads then cost shared
+// memory bank cycles instead of one L1 tag lookup per distinct line.  The
+// launch provides `smem_nodes` nodes of dynamic shared memory; a window that
+// does not fit (never, when the host sized it from the same extent) is read
+// from global memory instead.
+template <typename T, bool CHI2, bool SMEM>
+__global__ void __launch_bounds__(512)
 gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __restrict__ rho2,
               const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ re,
               const T* __restrict__ im, const T* __restrict__ w, int64_t M, int vec,
               cplx_t<T>* __restrict__ vis, double* __restrict__ partials,
-              unsigned* __restrict__ counter, double* __restrict__ chi2_out, int* __restrict__ err) {
+              unsigned* __restrict__ counter, double* __restrict__ chi2_out, int smem_nodes) {
   using C = cplx_t<T>;
   constexpr int W = Vec16<T>::W;
-  const Bounds bd = make_bounds(*rho2, p.Sd, p.N);
+  const Bounds bd = block_bounds(rho2, p.Sd, p.N);
+  const Window win = make_window(bd, p.N);
   typename Acc<T>::type acc;
+  const C* G = Gw;
+  if constexpr (SMEM) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sw = reinterpret_cast<C*>(smem_raw);
+    const int nodes = bd.nrw * bd.Kc;
+    if (nodes <= smem_nodes) {  // uniform over the grid
+      for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
+      __syncthreads();
+      G = sw;
+    }
+  }
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
@@ -444,17 +776,21 @@ gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __re
       load16(w, q, ww);
 #pragma unroll
       for (int e = 0; e < W; ++e) {
-        const C V = sample_point(Gw, bd, p, uu[e], vv[e], err);
+        const C V = SMEM ? sample_point<true>(G, win, p, uu[e], vv[e])
+                         : sample_point<false>(G, win, p, uu[e], vv[e]);
         const T dr = rr[e] - V.x, di = ii[e] - V.y;
         acc.add(ww[e] * (dr * dr + di * di));
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < W; ++e) vis[q * W + e] = sample_point(Gw, bd, p, uu[e], vv[e], err);
+      for (int e = 0; e < W; ++e)
+        vis[q * W + e] = SMEM ? sample_point<true>(G, win, p, uu[e], vv[e])
+                              : sample_point<false>(G, win, p, uu[e], vv[e]);
     }
   }
   for (int64_t k = nq * W + gtid; k < M; k += gstride) {
-    const C V = sample_point(Gw, bd, p, u[k], v[k], err);
+    const C V = SMEM ? sample_point<true>(G, win, p, u[k], v[k])
+                     : sample_point<false>(G, win, p, u[k], v[k]);
     if constexpr (CHI2) {
       const T dr = re[k] - V.x, di = im[k] - V.y;
       acc.add(w[k] * (dr * dr + di * di));
@@ -465,7 +801,7 @@ gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __re
   if constexpr (CHI2) {
     __shared__ double ws[32];
     __shared__ bool last;
-    const double bs = block_sum(acc.value(), ws);
+    const double bs = acc.block_total(ws);
     if (threadIdx.x == 0) {
       partials[blockIdx.x] = bs;
       __threadfence();
@@ -493,9 +829,23 @@ gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __re
 // ---------------------------------------------------------------------------
 namespace gal {
 
-constexpr int kMaxDynSmem = 227 * 1024;
+constexpr int kMaxDynSmem = 224 * 1024;  // leaves room for the kernels' static shared memory
+constexpr int kMaxWindowSmem = 200 * 1024;
 
 inline int row_threads_per_row(int N) { return N / 2 >= 8 ? N / 16 : 1; }
+
+// multiprocessor count of the current device (cached per device)
+inline int current_device_sms() {
+  static int cache[64] = {0};
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 1;
+  if (!cache[d]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+    cache[d] = n > 0 ? n : 1;
+  }
+  return cache[d];
+}
 inline int col_threads_per_col(int N) { return N >= 8 ? N / 8 : 1; }
 
 template <typename T> cudaError_t Launch<T>::init() {
@@ -506,16 +856,31 @@ template <typename T> cudaError_t Launch<T>::init() {
   if ((e = cudaFuncSetAttribute(row_pass_kernel<T, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)))
     return e;
+  // the gather also holds a little static shared memory (reduction scratch),
+  // so its dynamic budget stays below the per-block total
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
+    return e;
   return cudaFuncSetAttribute(col_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kMaxDynSmem);
 }
 
-template <typename T> int Launch<T>::gather_blocks_per_sm(bool chi2) {
+template <typename T> int Launch<T>::gather_blocks_per_sm(bool chi2, size_t window_smem) {
   int n = 0;
-  if (chi2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true>, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false>, 256, 0);
+  if (window_smem) {
+    if (chi2)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true>, 512, window_smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true>, 512, window_smem);
+  } else {
+    if (chi2)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, false>, 256, 0);
+  }
   return n < 1 ? 1 : n;
 }
 
@@ -548,10 +913,17 @@ cudaError_t Launch<T>::sweep(const T* I, const SweepParams& sp, int N, T* img, i
 
 template <typename T>
 cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& sp, int N,
-                                const void* tw, void* F1, const double* rho2, double S,
+                                const void* tw, void* F1, const double* rho2, double S, int* err,
                                 cudaStream_t st) {
   using C = cplx_t<T>;
   const int M = N / 2;
+  const bool al16 = I || (reinterpret_cast<uintptr_t>(image) & 15u) == 0;
+  if (M >= FftV<T>::V && al16) {
+    const cudaError_t e = row_fft3<T>(image, I, sp, N, tw, F1, rho2, S, err, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  const C* twc = static_cast<const C*>(tw);
+  C* out = static_cast<C*>(F1);
   const int tg = row_threads_per_row(N);
   int rpb = 256 / tg;
   if (rpb < 1) rpb = 1;
@@ -559,8 +931,6 @@ cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& s
   const int threads = tg * rpb;
   const size_t smem = (size_t)rpb * M * sizeof(C);
   const int grid = (N + rpb - 1) / rpb;
-  const C* twc = static_cast<const C*>(tw);
-  C* out = static_cast<C*>(F1);
   if (I)
     row_pass_kernel<T, true><<<grid, threads, smem, st>>>(nullptr, I, sweep_cast<T>(sp), N, twc,
                                                            out, rho2, S);
@@ -574,14 +944,20 @@ template <typename T>
 cudaError_t Launch<T>::col_pass(const void* F1, void* Gw, int N, const void* tw,
                                 const double* rho2, double S, cudaStream_t st) {
   using C = cplx_t<T>;
+  if (N >= FftV<T>::V) {
+    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  const int P = N / 2 + 1;
   const int tg = col_threads_per_col(N);
   int cpb = 256 / tg;
   if (cpb < 1) cpb = 1;
-  const int P = N / 2 + 1;
   if (cpb > P) cpb = P;
   const int threads = tg * cpb;
   const size_t smem = (size_t)cpb * (N + 1) * sizeof(C);
-  const int grid = (P + cpb - 1) / cpb;
+  int grid = (P + cpb - 1) / cpb;
+  const int cap = 2 * current_device_sms();
+  if (grid > cap) grid = cap;
   col_pass_kernel<T><<<grid, threads, smem, st>>>(static_cast<const C*>(F1), static_cast<C*>(Gw),
                                                   N, static_cast<const C*>(tw), rho2, S);
   return cudaGetLastError();
@@ -591,23 +967,34 @@ template <typename T>
 cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const double* rho2,
                               const T* u, const T* v, const T* re, const T* im, const T* w,
                               int64_t M, void* vis, double* partials, unsigned* counter,
-                              double* chi2, int* err, int blocks, cudaStream_t st) {
+                              double* chi2, size_t window_smem, int blocks, cudaStream_t st) {
   using C = cplx_t<T>;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   int vec = al16(u) && al16(v);
   if (chi2) vec = vec && al16(re) && al16(im) && al16(w);
   const GatherT<T> p = GatherT<T>::make(gp);
   const C* g = static_cast<const C*>(Gw);
+  const int nodes = (int)(window_smem / sizeof(C));
+  const int threads = window_smem ? 512 : 256;
   if (chi2) {
-    gather_kernel<T, true><<<blocks, 256, 0, st>>>(g, p, rho2, u, v, re, im, w, M, vec, nullptr,
-                                                   partials, counter, chi2, err);
+    if (window_smem)
+      gather_kernel<T, true, true><<<blocks, threads, window_smem, st>>>(
+          g, p, rho2, u, v, re, im, w, M, vec, nullptr, partials, counter, chi2, nodes);
+    else
+      gather_kernel<T, true, false><<<blocks, threads, 0, st>>>(
+          g, p, rho2, u, v, re, im, w, M, vec, nullptr, partials, counter, chi2, 0);
   } else {
-    int64_t need = (M + 255) / 256;
+    int64_t need = (M + threads - 1) / threads;
     if (need < 1) need = 1;
     const int grid = (int)(need < blocks ? need : blocks);
-    gather_kernel<T, false><<<grid, 256, 0, st>>>(g, p, rho2, u, v, nullptr, nullptr, nullptr, M,
-                                                  vec, static_cast<C*>(vis), nullptr, nullptr,
-                                                  nullptr, err);
+    if (window_smem)
+      gather_kernel<T, false, true><<<grid, threads, window_smem, st>>>(
+          g, p, rho2, u, v, nullptr, nullptr, nullptr, M, vec, static_cast<C*>(vis), nullptr,
+          nullptr, nullptr, nodes);
+    else
+      gather_kernel<T, false, false><<<grid, threads, 0, st>>>(
+          g, p, rho2, u, v, nullptr, nullptr, nullptr, M, vec, static_cast<C*>(vis), nullptr,
+          nullptr, nullptr, 0);
   }
   return cudaGetLastError();
 }

@@ -27,7 +27,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kOffTw = 0;
 constexpr size_t kOffF1 = kOffTw + align256(sizeof(float2) * kMaxN);
 constexpr size_t kOffGw = kOffF1 + align256(sizeof(float2) * kSpecElems);
-constexpr size_t kOffPartials = kOffGw + align256(sizeof(float2) * kSpecElems);
+constexpr size_t kOffPartials = kOffGw + align256(2 * sizeof(float2) * kSpecElems);
 constexpr size_t kOffRho2 = kOffPartials + align256(sizeof(double) * kMaxBlocks);
 constexpr size_t kOffCounter = kOffRho2 + 256;
 constexpr size_t kOffErr = kOffCounter + 256;
@@ -61,7 +61,7 @@ int setup_current_device(DeviceSetup** out) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
       return GAL_E_DEVICE;
-    int blocks = sms * gal::Launch<float>::gather_blocks_per_sm(true);
+    int blocks = sms * gal::Launch<float>::gather_blocks_per_sm(true, 0);
     s.gather_blocks = blocks < kMaxBlocks ? blocks : kMaxBlocks;
     s.aux_blocks = sms * 8;
     s.base = static_cast<unsigned char*>(p);
@@ -111,7 +111,7 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
     return GAL_E_CUDA;
   const double S = (double)nxy * dxy;
   gal::SweepParams none{};
-  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, cs) != cudaSuccess)
+  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, cs) != cudaSuccess)
     return GAL_E_CUDA;
   if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, cs) != cudaSuccess) return GAL_E_CUDA;
   gal::GatherParams gp;
@@ -122,7 +122,7 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
   gp.phy = dDec;
   gp.N = nxy;
   if (gal::Launch<float>::gather(Gw, gp, rho2, u, v, re, im, w, M, nullptr, partials, counter,
-                                 chi2_out, err, s->gather_blocks, cs) != cudaSuccess)
+                                 chi2_out, 0, s->gather_blocks, cs) != cudaSuccess)
     return GAL_E_CUDA;
   return GAL_OK;
 }
