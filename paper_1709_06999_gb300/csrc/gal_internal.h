@@ -21,11 +21,22 @@ struct GatherParams {
   int N;
 };
 
+// Byte ranges brought into L2 by extra blocks of the column pass, which
+// leaves HBM nearly idle; the gather streams them next.  Pointers 16-byte
+// aligned, sizes multiples of 16.
+struct L2Prefetch {
+  const void* ptr[5];
+  unsigned long long bytes[5];
+  int n;
+};
+
 // Host launchers, one explicit instantiation per precision.
 template <typename T> struct Launch {
   static cudaError_t init();  // kernel attributes; once per process
   // resident gather blocks per SM; window_smem > 0 selects the variant that
-  // stages the spectrum window (that many bytes) in shared memory
+  // stages the spectrum window (that many bytes) in shared memory.  The gather
+  // takes `edge` = false only when the window is known to be pruned (no uv
+  // point can reach the edge of the half spectrum).
   static int gather_blocks_per_sm(bool chi2, size_t window_smem);
   static cudaError_t twiddles(void* tw, int N, cudaStream_t st);
   static cudaError_t extent(const T* u, const T* v, int64_t M, double* rho2, int blocks,
@@ -36,12 +47,16 @@ template <typename T> struct Launch {
   static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                               const void* tw, void* F1, const double* rho2, double S, int* err,
                               cudaStream_t st);
+  // kc_hint: kept columns if the host knows them (0: unknown); pf: ranges to
+  // prefetch into L2 while the pass runs (may be null)
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
-                              const double* rho2, double S, cudaStream_t st);
+                              const double* rho2, double S, int kc_hint, const L2Prefetch* pf,
+                              cudaStream_t st);
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
                             int64_t M, void* vis, double* partials, unsigned* counter,
-                            double* chi2, size_t window_smem, int blocks, cudaStream_t st);
+                            double* chi2, size_t window_smem, bool edge, int blocks,
+                            cudaStream_t st);
 };
 
 // Compile-time-length FFT passes (gal_fft3.cuh), instantiated per precision in
@@ -52,6 +67,6 @@ cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, c
                      void* F1, const double* rho2, double S, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     cudaStream_t st);
+                     int kc_hint, const L2Prefetch* pf, cudaStream_t st);
 
 }  // namespace gal

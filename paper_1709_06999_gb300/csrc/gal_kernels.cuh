@@ -394,10 +394,38 @@ row_fft3_kernel(const T* __restrict__ image, const T* __restrict__ I, SweepT<T> 
 // of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
 // r0 + nrw - 1 are written to the window Gw (nrw x Kc).  When the window is
 // pruned, only the kept frequencies +-j are evaluated.
+// Blocks col_blocks and above only issue L2 bulk prefetches of pf (64 KiB per
+// instruction, interleaved over the ranges so each is fetched front first).
+__device__ __forceinline__ void l2_prefetch(const L2Prefetch& pf, int tid, int nthreads) {
+  constexpr unsigned long long CH = 64ull * 1024;
+  unsigned long long nch[5], maxc = 0;
+  for (int a = 0; a < pf.n; ++a) {
+    nch[a] = (pf.bytes[a] + CH - 1) / CH;
+    maxc = nch[a] > maxc ? nch[a] : maxc;
+  }
+  for (unsigned long long g = tid; g < maxc * pf.n; g += nthreads) {
+    const int a = (int)(g % pf.n);
+    const unsigned long long k = g / pf.n;
+    if (k >= nch[a]) continue;
+    const unsigned long long off = k * CH;
+    const unsigned long long len = pf.bytes[a] - off < CH ? pf.bytes[a] - off : CH;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     static_cast<const char*>(pf.ptr[a]) + off),
+                 "r"((unsigned)len)
+                 : "memory");
+  }
+}
+
 template <typename T, int LG>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads)
 col_fft3_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gw,
-                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S) {
+                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S,
+                int col_blocks, L2Prefetch pf) {
+  if ((int)blockIdx.x >= col_blocks) {
+    l2_prefetch(pf, (blockIdx.x - col_blocks) * blockDim.x + threadIdx.x,
+                (gridDim.x - col_blocks) * blockDim.x);
+    return;
+  }
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
@@ -417,7 +445,7 @@ col_fft3_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gw,
   C* A = base + (size_t)g * RS;
   C* B = base + (size_t)(G + g) * RS;
   auto sync = [] { __syncthreads(); };
-  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += gridDim.x * G) {
+  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += col_blocks * G) {
     const int c = c0 + g;
     const bool act = c < bd.Kc;
     C v[V];
@@ -486,6 +514,9 @@ template <typename T> struct GatherT;
 // dRA and dDec (turns per wavelength).  All four are float-float.
 template <> struct GatherT<float> {
   ff A, B, PX, PY;
+  // the same constants broadcast to both lanes of an f32x2 pair (read by the
+  // two-point path straight from the kernel parameters)
+  float2 Ah, Al, nAh, Bh, Bl, nBh, nBl, PXh, PXl, PYh, PYl, m1, twopi;
   double Sd;
   int N;
   __host__ static GatherT make(const GatherParams& g) {
@@ -494,6 +525,20 @@ template <> struct GatherT<float> {
     r.B = ff_split(g.spa * g.S);
     r.PX = ff_split(g.phx);
     r.PY = ff_split(g.phy);
+    auto b2 = [](float x) { return make_float2(x, x); };
+    r.Ah = b2(r.A.hi);
+    r.Al = b2(r.A.lo);
+    r.nAh = b2(-r.A.hi);
+    r.Bh = b2(r.B.hi);
+    r.Bl = b2(r.B.lo);
+    r.nBh = b2(-r.B.hi);
+    r.nBl = b2(-r.B.lo);
+    r.PXh = b2(r.PX.hi);
+    r.PXl = b2(r.PX.lo);
+    r.PYh = b2(r.PY.hi);
+    r.PYl = b2(r.PY.lo);
+    r.m1 = b2(-1.f);
+    r.twopi = b2(6.28318530717958647692f);
     r.Sd = g.S;
     r.N = g.N;
     return r;
@@ -545,10 +590,13 @@ template <bool SMEM, typename C> __device__ __forceinline__ C ld_node(const C* p
   else return __ldg(p);
 }
 
-template <bool SMEM>
+// EDGE: clamp positions beyond the node range to the edge (App. D).  Needed
+// only when the window is the whole half spectrum; for a pruned window no
+// point can reach its edge, and the index clamps below only keep every read
+// in bounds for non-finite input (whose result is NaN through the phase).
+template <bool SMEM, bool EDGE>
 __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__ Gp, const Window& w,
                                                const GatherT<float>& p, float u, float v) {
-  if (!(isfinite(u) && isfinite(v))) return make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
   float xae, xbe, yae, ybe;
   const float xa = prod_hi_lo(u, p.A, xae), xb = prod_hi_lo(v, p.B, xbe);
   const float ya = prod_hi_lo(u, p.B, yae), yb = prod_hi_lo(v, p.A, ybe);
@@ -566,26 +614,32 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
     yh = -yh;
     yl = -yl;
   }
-  float cf, fu, rf, fv;
-  split_cell(xh, xl, cf, fu);
-  split_cell(yh, yl, rf, fv);
-  int c = (int)cf;
-  if (c < 0) {
-    c = 0;
-    fu = 0.f;
-  } else if (c > w.cmax) {
-    c = w.cmax;
-    fu = 1.f;
+  // cell = floor(hi); fraction = (hi - cell) + lo, saturated to [0, 1]: when
+  // hi sits within |lo| of an integer the neighbouring cell would be exact,
+  // and the saturated fraction differs from it by at most |lo| (one ulp)
+  const float cf = floorf(xh), rf = floorf(yh);
+  float fu = __saturatef((xh - cf) + xl);
+  float fv = __saturatef((yh - rf) + yl);
+  int c = (int)fminf(cf, 32768.f);
+  int r = (int)fmaxf(fminf(rf, 32768.f), -32768.f) + w.rofs;
+  if constexpr (EDGE) {
+    if (c > w.cmax) {
+      c = w.cmax;
+      fu = 1.f;
+    }
+    if (r < 0) {
+      r = 0;
+      fv = 0.f;
+    } else if (r > w.rmax) {
+      r = w.rmax;
+      fv = 1.f;
+    }
+    c = max(c, 0);
+  } else {
+    c = min(max(c, 0), w.cmax);
+    r = min(max(r, 0), w.rmax);
   }
-  int r = (int)rf + w.rofs;
-  if (r < 0) {
-    r = 0;
-    fv = 0.f;
-  } else if (r > w.rmax) {
-    r = w.rmax;
-    fv = 1.f;
-  }
-  const float2* g = Gp + (size_t)r * w.pitch + c;
+  const float2* g = Gp + r * w.pitch + c;
   const float2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
   const float2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
   const float ar = fmaf(fu, g01.x - g00.x, g00.x), ai = fmaf(fu, g01.y - g00.y, g00.y);
@@ -605,6 +659,139 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
   return make_float2(Vr * cs - Vi * sn, Vr * sn + Vi * cs);
 }
 
+// ---------------------------------------------------------------------------
+// float path, two uv points per evaluation: every per-point FP32 operation
+// runs as one packed f32x2 instruction (sm_100+: two FP32 results per issue
+// slot), lane .x for the first point and .y for the second.  Subtractions
+// are fma(a, -1, b), which is exact, so the error-free transformations keep
+// their guarantees.  Same arithmetic as sample_point<float>.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Round to nearest integer on the FMA pipe: for |x| < 2^22, x + 1.5 2^23
+// rounds x to an integer in the low mantissa bits.  rint_fma(x) is exact there;
+// for larger |x| it returns a value within 1 of x that is exactly
+// representable, so x - rint_fma(x) is still computed exactly (|.| <= 1).
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ float rint_fma(float x) { return __fsub_rn(__fadd_rn(x, kMagic), kMagic); }
+__device__ __forceinline__ float2 rint_fma2(float2 x) {
+  return __fadd2_rn(__fadd2_rn(x, make_float2(kMagic, kMagic)), make_float2(-kMagic, -kMagic));
+}
+// floor(x) for |x| < 2^22, as float and int, without the XU pipe
+__device__ __forceinline__ int floor_fma(float x, float& fl) {
+  const float t = __fadd_rn(x, kMagic);
+  int i = __float_as_int(t) - 0x4B400000;
+  float r = __fsub_rn(t, kMagic);
+  if (r > x) {
+    r -= 1.f;
+    i -= 1;
+  }
+  fl = r;
+  return i;
+}
+
+using Pair2Const = GatherT<float>;  // the broadcast pairs live in the kernel parameters
+
+// x * c exactly as hi + lo for c = ch + cl: hi = x ch, lo = (x ch - hi) + x cl.
+// nch = -ch gives -hi without a negation instruction.
+__device__ __forceinline__ float2 prod2(float2 x, float2 ch, float2 nch, float2 cl, float2& lo) {
+  const float2 hi = mul2(x, ch);
+  const float2 nhi = mul2(x, nch);
+  lo = fma2(x, cl, fma2(x, ch, nhi));
+  return hi;
+}
+
+// TwoSum of two pairs: a + b = s + e exactly
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 m1, float2& e) {
+  const float2 s = add2(a, b);
+  const float2 bb = fma2(a, m1, s);   // s - a
+  const float2 t = fma2(bb, m1, s);   // s - bb
+  e = add2(fma2(t, m1, a), fma2(bb, m1, b));  // (a - t) + (b - bb)
+  return s;
+}
+
+template <bool SMEM, bool EDGE>
+__device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const Window& w, float xh,
+                                           float xl, float yh, float yl, bool neg, float2& V) {
+  // positions are grid offsets (|.| <= 8192), so the FMA-pipe floor applies;
+  // non-finite input yields an arbitrary cell, clamped below, and NaN through
+  // the phase
+  float cf, rf;
+  int c = floor_fma(xh, cf);
+  int r = floor_fma(yh, rf) + w.rofs;
+  float fu = __saturatef((xh - cf) + xl);
+  float fv = __saturatef((yh - rf) + yl);
+  if constexpr (EDGE) {
+    if (c > w.cmax) {
+      c = w.cmax;
+      fu = 1.f;
+    }
+    if (r < 0) {
+      r = 0;
+      fv = 0.f;
+    } else if (r > w.rmax) {
+      r = w.rmax;
+      fv = 1.f;
+    }
+    c = max(c, 0);
+  } else {
+    c = min(max(c, 0), w.cmax);
+    r = min(max(r, 0), w.rmax);
+  }
+  const float2* g = G + r * w.pitch + c;
+  const float2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
+  const float2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
+  const float2 m1 = pk(-1.f, -1.f);
+  const float2 FU = pk(fu, fu), FV = pk(fv, fv);
+  const float2 a = fma2(FU, fma2(g00, m1, g01), g00);
+  const float2 b = fma2(FU, fma2(g10, m1, g11), g10);
+  V = fma2(FV, fma2(a, m1, b), a);
+  if (neg) V.y = -V.y;
+}
+
+template <bool SMEM, bool EDGE>
+__device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const Window& w,
+                                            const Pair2Const& k, float2 U, float2 Vv, float2& V0,
+                                            float2& V1) {
+  // x = u A - v B, y = u B + v A, both lanes at once, as hi + lo
+  float2 e1, e2, e3, e4, ex, ey;
+  const float2 p1 = prod2(U, k.Ah, k.nAh, k.Al, e1);    //  u A
+  const float2 p2 = prod2(Vv, k.nBh, k.Bh, k.nBl, e2);  // -v B
+  const float2 xh2 = two_sum2(p1, p2, k.m1, ex);
+  const float2 xl2 = add2(ex, add2(e1, e2));
+  const float2 p3 = prod2(U, k.Bh, k.nBh, k.Bl, e3);    //  u B
+  const float2 p4 = prod2(Vv, k.Ah, k.nAh, k.Al, e4);   //  v A
+  const float2 yh2 = two_sum2(p3, p4, k.m1, ey);
+  const float2 yl2 = add2(ey, add2(e3, e4));
+  // phase in turns: (u dRA, v dDec) per lane, each reduced by its nearest
+  // integer, then summed with the low parts
+  float2 pe1, pe2;
+  const float2 pa = mul2(U, k.PXh), pb = mul2(Vv, k.PYh);
+  pe1 = fma2(U, k.PXl, fma2(U, k.PXh, mul2(pa, k.m1)));
+  pe2 = fma2(Vv, k.PYl, fma2(Vv, k.PYh, mul2(pb, k.m1)));
+  const float2 ra = fma2(rint_fma2(pa), k.m1, pa);  // exact, |ra| <= 1
+  const float2 rb = fma2(rint_fma2(pb), k.m1, pb);
+  float2 f = add2(add2(ra, rb), add2(pe1, pe2));
+  f = fma2(rint_fma2(f), k.m1, f);  // |f| <= 1/2
+  const float2 ang = mul2(f, k.twopi);  // |angle| <= pi
+  float s0, c0, s1, c1;
+  __sincosf(ang.x, &s0, &c0);
+  __sincosf(ang.y, &s1, &c1);
+  // Hermitian fold per lane
+  const bool n0 = xh2.x < 0.f, n1 = xh2.y < 0.f;
+  const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
+  const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
+  float2 A0, A1;
+  cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
+  cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
+  // rotate by the phase: V (c + i s) = c V + s (-Vi, Vr)
+  V0 = fma2(pk(s0, s0), pk(-A0.y, A0.x), mul2(pk(c0, c0), A0));
+  V1 = fma2(pk(s1, s1), pk(-A1.y, A1.x), mul2(pk(c1, c1), A1));
+}
+
 // cell of the position ofs + x (x relative to the window's origin row or
 // column ofs), clamped to the window's node range [0, last + 1].  The floor
 // is taken of x itself so the result does not depend on the window's size.
@@ -622,7 +809,7 @@ __device__ __forceinline__ void cell_d(double x, int ofs, int last, int& c, doub
   }
 }
 
-template <bool SMEM>
+template <bool SMEM, bool EDGE>
 __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict__ Gp, const Window& w,
                                                 const GatherT<double>& p, double u, double v) {
   if (!(isfinite(u) && isfinite(v)))
@@ -739,64 +926,131 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
 // launch provides `smem_nodes` nodes of dynamic shared memory; a window that
 // does not fit (never, when the host sized it from the same extent) is read
 // from global memory instead.
-template <typename T, bool CHI2, bool SMEM>
-__global__ void __launch_bounds__(512)
-gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __restrict__ rho2,
-              const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ re,
-              const T* __restrict__ im, const T* __restrict__ w, int64_t M, int vec,
-              cplx_t<T>* __restrict__ vis, double* __restrict__ partials,
-              unsigned* __restrict__ counter, double* __restrict__ chi2_out, int smem_nodes) {
+
+// Loop over this thread's uv points, reading the window nodes through G
+// (SMEM: G points into shared memory).  Vector part software-pipelined: the
+// next group's loads are in flight while the current group is evaluated.
+template <typename T, bool CHI2, bool SMEM, bool EDGE, typename ACC>
+__device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
+                                              const GatherT<T>& p, const T* __restrict__ u,
+                                              const T* __restrict__ v, const T* __restrict__ re,
+                                              const T* __restrict__ im, const T* __restrict__ w,
+                                              int64_t M, int vec, cplx_t<T>* __restrict__ vis,
+                                              ACC& acc) {
   using C = cplx_t<T>;
   constexpr int W = Vec16<T>::W;
-  const Bounds bd = block_bounds(rho2, p.Sd, p.N);
-  const Window win = make_window(bd, p.N);
-  typename Acc<T>::type acc;
-  const C* G = Gw;
-  if constexpr (SMEM) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sw = reinterpret_cast<C*>(smem_raw);
-    const int nodes = bd.nrw * bd.Kc;
-    if (nodes <= smem_nodes) {  // uniform over the grid
-      for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
-      __syncthreads();
-      G = sw;
-    }
-  }
+  auto point = [&](T uu, T vv) { return sample_point<SMEM, EDGE>(G, win, p, uu, vv); };
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
-  for (int64_t q = gtid; q < nq; q += gstride) {
-    T uu[W], vv[W];
+  if (gtid < nq) {
+    int64_t q = gtid;
+    T uu[W], vv[W], rr[W], ii[W], ww[W];
     load16(u, q, uu);
     load16(v, q, vv);
     if constexpr (CHI2) {
-      T rr[W], ii[W], ww[W];
       load16(re, q, rr);
       load16(im, q, ii);
       load16(w, q, ww);
+    }
+    while (true) {
+      const int64_t qn = q + gstride;
+      const bool more = qn < nq;
+      T un[W], vn[W], rn[W], in_[W], wn[W];
+      if (more) {
+        load16(u, qn, un);
+        load16(v, qn, vn);
+        if constexpr (CHI2) {
+          load16(re, qn, rn);
+          load16(im, qn, in_);
+          load16(w, qn, wn);
+        }
+      }
+      C Vs[W];
+      if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int e = 0; e < W; e += 2)
+          sample_pair<SMEM, EDGE>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]), Vs[e],
+                                  Vs[e + 1]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < W; ++e) Vs[e] = point(uu[e], vv[e]);
+      }
+      if constexpr (CHI2) {
+        T part = (T)0;
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+          const T dr = rr[e] - Vs[e].x, di = ii[e] - Vs[e].y;
+          part += ww[e] * (dr * dr + di * di);
+        }
+        acc.add(part);
+      } else {
+#pragma unroll
+        for (int e = 0; e < W; ++e) vis[q * W + e] = Vs[e];
+      }
+      if (!more) break;
+      q = qn;
 #pragma unroll
       for (int e = 0; e < W; ++e) {
-        const C V = SMEM ? sample_point<true>(G, win, p, uu[e], vv[e])
-                         : sample_point<false>(G, win, p, uu[e], vv[e]);
-        const T dr = rr[e] - V.x, di = ii[e] - V.y;
-        acc.add(ww[e] * (dr * dr + di * di));
+        uu[e] = un[e];
+        vv[e] = vn[e];
+        if constexpr (CHI2) {
+          rr[e] = rn[e];
+          ii[e] = in_[e];
+          ww[e] = wn[e];
+        }
       }
-    } else {
-#pragma unroll
-      for (int e = 0; e < W; ++e)
-        vis[q * W + e] = SMEM ? sample_point<true>(G, win, p, uu[e], vv[e])
-                              : sample_point<false>(G, win, p, uu[e], vv[e]);
     }
   }
   for (int64_t k = nq * W + gtid; k < M; k += gstride) {
-    const C V = SMEM ? sample_point<true>(G, win, p, u[k], v[k])
-                     : sample_point<false>(G, win, p, u[k], v[k]);
+    const C V = point(u[k], v[k]);
     if constexpr (CHI2) {
       const T dr = re[k] - V.x, di = im[k] - V.y;
       acc.add(w[k] * (dr * dr + di * di));
     } else {
       vis[k] = V;
     }
+  }
+}
+
+template <typename T, bool CHI2, bool SMEM, bool EDGE>
+__global__ void __launch_bounds__(256, 3)
+gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __restrict__ rho2,
+              const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ re,
+              const T* __restrict__ im, const T* __restrict__ w, int64_t M, int vec,
+              cplx_t<T>* __restrict__ vis, double* __restrict__ partials,
+              unsigned* __restrict__ counter, double* __restrict__ chi2_out, int smem_nodes) {
+  using C = cplx_t<T>;
+  const Bounds bd = block_bounds(rho2, p.Sd, p.N);
+  const Window win = make_window(bd, p.N);
+  typename Acc<T>::type acc;
+  if constexpr (SMEM) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sw = reinterpret_cast<C*>(smem_raw);
+    const int nodes = bd.nrw * bd.Kc;
+    if (nodes <= smem_nodes) {  // uniform over the grid; always true when sized by the host
+      // one bulk copy of the window (rounded up to 16 bytes; the window
+      // buffer and the shared allocation both have the slack)
+      __shared__ __align__(8) uint64_t wbar;
+      const uint32_t bytes = ((uint32_t)(nodes * sizeof(C)) + 15u) & ~15u;
+      if (threadIdx.x == 0) {
+        mbar_init(&wbar, 1);
+        mbar_init_fence();
+        mbar_arrive_expect_tx(&wbar, bytes);
+        bulk_load(sw, Gw, bytes, &wbar);
+      }
+      __syncthreads();
+      const bool ok = mbar_wait(&wbar, 0);
+      if (__syncthreads_or(!ok)) {  // never expected: fall back to plain loads
+        for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
+        __syncthreads();
+      }
+      gather_points<T, CHI2, true, EDGE>(sw, win, p, u, v, re, im, w, M, vec, vis, acc);
+    } else {
+      gather_points<T, CHI2, false, EDGE>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc);
+    }
+  } else {
+    gather_points<T, CHI2, false, EDGE>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc);
   }
   if constexpr (CHI2) {
     __shared__ double ws[32];
@@ -858,10 +1112,16 @@ template <typename T> cudaError_t Launch<T>::init() {
     return e;
   // the gather also holds a little static shared memory (reduction scratch),
   // so its dynamic budget stays below the per-block total
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
   return cudaFuncSetAttribute(col_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -872,14 +1132,16 @@ template <typename T> int Launch<T>::gather_blocks_per_sm(bool chi2, size_t wind
   int n = 0;
   if (window_smem) {
     if (chi2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true>, 512, window_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true, true>, 256,
+                                                    window_smem);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true>, 512, window_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true, true>, 256,
+                                                    window_smem);
   } else {
     if (chi2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false, true>, 256, 0);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, false>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, false, true>, 256, 0);
   }
   return n < 1 ? 1 : n;
 }
@@ -942,10 +1204,11 @@ cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& s
 
 template <typename T>
 cudaError_t Launch<T>::col_pass(const void* F1, void* Gw, int N, const void* tw,
-                                const double* rho2, double S, cudaStream_t st) {
+                                const double* rho2, double S, int kc_hint, const L2Prefetch* pf,
+                                cudaStream_t st) {
   using C = cplx_t<T>;
   if (N >= FftV<T>::V) {
-    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, st);
+    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, pf, st);
     if (e != cudaErrorNotSupported) return e;
   }
   const int P = N / 2 + 1;
@@ -967,7 +1230,8 @@ template <typename T>
 cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const double* rho2,
                               const T* u, const T* v, const T* re, const T* im, const T* w,
                               int64_t M, void* vis, double* partials, unsigned* counter,
-                              double* chi2, size_t window_smem, int blocks, cudaStream_t st) {
+                              double* chi2, size_t window_smem, bool edge, int blocks,
+                              cudaStream_t st) {
   using C = cplx_t<T>;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   int vec = al16(u) && al16(v);
@@ -975,26 +1239,31 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
   const GatherT<T> p = GatherT<T>::make(gp);
   const C* g = static_cast<const C*>(Gw);
   const int nodes = (int)(window_smem / sizeof(C));
-  const int threads = window_smem ? 512 : 256;
-  if (chi2) {
-    if (window_smem)
-      gather_kernel<T, true, true><<<blocks, threads, window_smem, st>>>(
-          g, p, rho2, u, v, re, im, w, M, vec, nullptr, partials, counter, chi2, nodes);
-    else
-      gather_kernel<T, true, false><<<blocks, threads, 0, st>>>(
-          g, p, rho2, u, v, re, im, w, M, vec, nullptr, partials, counter, chi2, 0);
-  } else {
+  const int threads = 256;
+  int grid = blocks;
+  if (!chi2) {
     int64_t need = (M + threads - 1) / threads;
     if (need < 1) need = 1;
-    const int grid = (int)(need < blocks ? need : blocks);
+    if (need < grid) grid = (int)need;
+  }
+  C* vo = static_cast<C*>(vis);
+  auto go = [&](auto kern, size_t smem) {
+    kern<<<grid, threads, smem, st>>>(g, p, rho2, u, v, re, im, w, M, vec, vo, partials, counter,
+                                      chi2, nodes);
+  };
+  if (chi2) {
     if (window_smem)
-      gather_kernel<T, false, true><<<grid, threads, window_smem, st>>>(
-          g, p, rho2, u, v, nullptr, nullptr, nullptr, M, vec, static_cast<C*>(vis), nullptr,
-          nullptr, nullptr, nodes);
+      edge ? go(gather_kernel<T, true, true, true>, window_smem)
+           : go(gather_kernel<T, true, true, false>, window_smem);
     else
-      gather_kernel<T, false, false><<<grid, threads, 0, st>>>(
-          g, p, rho2, u, v, nullptr, nullptr, nullptr, M, vec, static_cast<C*>(vis), nullptr,
-          nullptr, nullptr, 0);
+      edge ? go(gather_kernel<T, true, false, true>, 0) : go(gather_kernel<T, true, false, false>, 0);
+  } else {
+    if (window_smem)
+      edge ? go(gather_kernel<T, false, true, true>, window_smem)
+           : go(gather_kernel<T, false, true, false>, window_smem);
+    else
+      edge ? go(gather_kernel<T, false, false, true>, 0)
+           : go(gather_kernel<T, false, false, false>, 0);
   }
   return cudaGetLastError();
 }

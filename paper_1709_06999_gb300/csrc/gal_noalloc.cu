@@ -113,7 +113,8 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
   gal::SweepParams none{};
   if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, cs) != cudaSuccess)
     return GAL_E_CUDA;
-  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, cs) != cudaSuccess) return GAL_E_CUDA;
+  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, 0, nullptr, cs) != cudaSuccess)
+    return GAL_E_CUDA;
   gal::GatherParams gp;
   gp.cpa = std::cos(PA);
   gp.spa = std::sin(PA);
@@ -122,7 +123,7 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
   gp.phy = dDec;
   gp.N = nxy;
   if (gal::Launch<float>::gather(Gw, gp, rho2, u, v, re, im, w, M, nullptr, partials, counter,
-                                 chi2_out, 0, s->gather_blocks, cs) != cudaSuccess)
+                                 chi2_out, 0, true, s->gather_blocks, cs) != cudaSuccess)
     return GAL_E_CUDA;
   return GAL_OK;
 }
