@@ -16,6 +16,8 @@
 #include "gal_fft2.cuh"
 #include "gal_fft3.cuh"
 #include "gal_tma.cuh"
+
+#include <limits>
 #include "gal_internal.h"
 
 namespace gal {
@@ -928,8 +930,7 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
 // from global memory instead.
 
 // Loop over this thread's uv points, reading the window nodes through G
-// (SMEM: G points into shared memory).  Vector part software-pipelined: the
-// next group's loads are in flight while the current group is evaluated.
+// (SMEM: G points into shared memory).
 template <typename T, bool CHI2, bool SMEM, bool EDGE, typename ACC>
 __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
                                               const GatherT<T>& p, const T* __restrict__ u,
@@ -943,8 +944,7 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
-  if (gtid < nq) {
-    int64_t q = gtid;
+  for (int64_t q = gtid; q < nq; q += gstride) {
     T uu[W], vv[W], rr[W], ii[W], ww[W];
     load16(u, q, uu);
     load16(v, q, vv);
@@ -953,53 +953,27 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
       load16(im, q, ii);
       load16(w, q, ww);
     }
-    while (true) {
-      const int64_t qn = q + gstride;
-      const bool more = qn < nq;
-      T un[W], vn[W], rn[W], in_[W], wn[W];
-      if (more) {
-        load16(u, qn, un);
-        load16(v, qn, vn);
-        if constexpr (CHI2) {
-          load16(re, qn, rn);
-          load16(im, qn, in_);
-          load16(w, qn, wn);
-        }
-      }
-      C Vs[W];
-      if constexpr (sizeof(T) == 4) {
+    C Vs[W];
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-        for (int e = 0; e < W; e += 2)
-          sample_pair<SMEM, EDGE>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]), Vs[e],
-                                  Vs[e + 1]);
-      } else {
+      for (int e = 0; e < W; e += 2)
+        sample_pair<SMEM, EDGE>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]), Vs[e],
+                                Vs[e + 1]);
+    } else {
 #pragma unroll
-        for (int e = 0; e < W; ++e) Vs[e] = point(uu[e], vv[e]);
-      }
-      if constexpr (CHI2) {
-        T part = (T)0;
-#pragma unroll
-        for (int e = 0; e < W; ++e) {
-          const T dr = rr[e] - Vs[e].x, di = ii[e] - Vs[e].y;
-          part += ww[e] * (dr * dr + di * di);
-        }
-        acc.add(part);
-      } else {
-#pragma unroll
-        for (int e = 0; e < W; ++e) vis[q * W + e] = Vs[e];
-      }
-      if (!more) break;
-      q = qn;
+      for (int e = 0; e < W; ++e) Vs[e] = point(uu[e], vv[e]);
+    }
+    if constexpr (CHI2) {
+      T part = (T)0;
 #pragma unroll
       for (int e = 0; e < W; ++e) {
-        uu[e] = un[e];
-        vv[e] = vn[e];
-        if constexpr (CHI2) {
-          rr[e] = rn[e];
-          ii[e] = in_[e];
-          ww[e] = wn[e];
-        }
+        const T dr = rr[e] - Vs[e].x, di = ii[e] - Vs[e].y;
+        part += ww[e] * (dr * dr + di * di);
       }
+      acc.add(part);
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e) vis[q * W + e] = Vs[e];
     }
   }
   for (int64_t k = nq * W + gtid; k < M; k += gstride) {
@@ -1013,8 +987,12 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   }
 }
 
+// block shape: one 1024-thread block per SM when the window is staged in
+// shared memory (32 warps share one copy), 256-thread blocks otherwise
+template <bool SMEM> constexpr int gather_threads() { return SMEM ? 1024 : 256; }
+
 template <typename T, bool CHI2, bool SMEM, bool EDGE>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 1 : 3)
 gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __restrict__ rho2,
               const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ re,
               const T* __restrict__ im, const T* __restrict__ w, int64_t M, int vec,
@@ -1047,7 +1025,16 @@ gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __re
       }
       gather_points<T, CHI2, true, EDGE>(sw, win, p, u, v, re, im, w, M, vec, vis, acc);
     } else {
-      gather_points<T, CHI2, false, EDGE>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc);
+      // the host sizes the shared window from the same extent, so this is
+      // never taken; the result is NaN rather than a read out of bounds
+      const T nan = std::numeric_limits<T>::quiet_NaN();
+      if constexpr (CHI2) {
+        acc.add(nan);
+      } else {
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+             k += (int64_t)gridDim.x * blockDim.x)
+          vis[k] = mkc(nan, nan);
+      }
     }
   } else {
     gather_points<T, CHI2, false, EDGE>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc);
@@ -1132,11 +1119,11 @@ template <typename T> int Launch<T>::gather_blocks_per_sm(bool chi2, size_t wind
   int n = 0;
   if (window_smem) {
     if (chi2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true, true>, 256,
-                                                    window_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true, true>,
+                                                    gather_threads<true>(), window_smem);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true, true>, 256,
-                                                    window_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true, true>,
+                                                    gather_threads<true>(), window_smem);
   } else {
     if (chi2)
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false, true>, 256, 0);
@@ -1239,7 +1226,7 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
   const GatherT<T> p = GatherT<T>::make(gp);
   const C* g = static_cast<const C*>(Gw);
   const int nodes = (int)(window_smem / sizeof(C));
-  const int threads = 256;
+  const int threads = window_smem ? gather_threads<true>() : gather_threads<false>();
   int grid = blocks;
   if (!chi2) {
     int64_t need = (M + threads - 1) / threads;
