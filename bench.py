@@ -5,7 +5,8 @@ FFT, gather + phase + chi-square): nxy = 4096 float32 image of three random
 elliptical Gaussians plus an exp(-r/0.2") disc, dxy = 0.002", M = 5e6
 ALMA-like uv points (43 antennas, 60 hour angles, 93 channels around 100 GHz),
 random dRA/dDec in +-0.1" and PA in [0, pi).  Inputs are resident in HBM; L2
-is flushed (a 256 MiB write) before every timed step; each step is timed on
+is flushed before every timed step (a 256 MiB write, then a 256 MiB read that
+takes the write-back of the dirty lines out of the timed region); each step is timed on
 the device with CUDA events on the launching stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -38,8 +39,9 @@ WORKLOAD = "chi2_image nxy=4096 dxy=0.002as M=5e6 ALMA-like uv, 3 Gaussians + ex
 NXY, M_UV = 4096, 5_000_000
 L2_FLUSH_BYTES = 256 << 20
 STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
-KERNELS = {1: "row_pass_kernel<float,false>", 2: "col_pass_kernel<float>",
-           3: "gather_kernel<float,true>"}
+# kernels launched for this workload (template arguments as ncu prints them)
+KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0>", 2: "col_fft3_kernel<float, 12>",
+           3: "gather_kernel<float, 1, 1, 0>"}
 
 
 def algorithmic_bytes(stage: int, nxy: int, M: int, Kc: int, nrw: int) -> float:
@@ -248,6 +250,7 @@ def run_gpu(args):
     obs = ctx.register(u, v, re, im, w)
     out = torch.empty((), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     # a few parameter sets, as successive MCMC steps would use
     prng = np.random.default_rng(11 + rank)
@@ -259,9 +262,24 @@ def run_gpu(args):
         dRA, dDec, PA = params[i % len(params)]
         ctx.chi2_image(img, p.dxy, obs, dRA, dDec, PA, out=out)
 
+    def flush_l2():
+        # write a buffer larger than L2 (evicts every line of the workload),
+        # then read a second one so that the write-back of those dirty lines
+        # happens here and not inside the next timed step
+        flush.zero_()
+        flush_rd.sum(dtype=torch.int32)
+
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize(dev)
+    # calibration (untimed): which stage dominates the step
+    ctx.set_stage_timing(True)
+    for i in range(3):
+        flush_l2()
+        step(i)
+    cal = ctx.stage_times()
+    ctx.set_stage_timing(False)
+    dom = max((1, 2, 3), key=lambda s: cal[s][0] / max(cal[s][1], 1))
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -269,10 +287,11 @@ def run_gpu(args):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
-    ctx.set_stage_timing(True)
+    # inside the timed region only the dominant kernel is bracketed by events
+    ctx.set_stage_timing(True, stages=[dom])
     with ClockSampler(dev.index if world == 1 else local) as clk:
         for i in range(args.steps):
-            flush.zero_()
+            flush_l2()
             ev[i][0].record(stream)
             step(i)
             ev[i][1].record(stream)
@@ -327,7 +346,6 @@ def run_gpu(args):
     rho = float(np.sqrt(np.max(p.u ** 2 + p.v ** 2)))
     Kc, nrw = window(rho, NXY * p.dxy, NXY)
     avg = {s: (stage[s][0] / stage[s][1]) for s in (1, 2, 3) if stage[s][1]}
-    dom = max(avg, key=avg.get)
     alg = algorithmic_bytes(dom, NXY, M_UV, Kc, nrw)
     achieved = alg / (avg[dom] * 1e-3) / 1e9
     peak, peak_kind = peaks()
@@ -342,7 +360,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV, "l2": "flushed before every step",
+        "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV, "l2": "flushed before every step (256 MiB write + 256 MiB read)",
                    "kept_window": {"columns": Kc, "rows": nrw}, "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * NXY * NXY,
                 "d2h_bytes_per_step": 8,
@@ -352,8 +370,10 @@ def run_gpu(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": alg,
                      "avg_launch_us": 1000 * avg[dom]},
-        "stages_us": {STAGES[s]: round(1000 * stage[s][0] / stage[s][1], 2)
-                      for s in range(4) if stage[s][1]},
+        "stages_us": {STAGES[s]: round(1000 * cal[s][0] / cal[s][1], 2)
+                      for s in range(4) if cal[s][1]},
+        "stages_note": "per-stage event times from 3 untimed calibration steps; "
+                       "in the timed steps only the dominant stage carries events",
         "fp64_plain": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
                        "note": "same workload through the float64 entry point, single calls"},
         "clocks": clk.summary(),

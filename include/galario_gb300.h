@@ -75,11 +75,15 @@ const char* gal_last_cuda_error(const gal_ctx* ctx);
 int gal_check(gal_ctx* ctx);
 /* Number of kernels this context has launched since creation. */
 uint64_t gal_launch_count(const gal_ctx* ctx);
-/* Per-stage device timing.  When enabled, each call brackets its kernels with
- * CUDA events; gal_stage_times synchronises and returns, per stage, the summed
- * milliseconds and the number of launches since timing was (re)enabled.
- * Stages: 0 uv extent, 1 row FFT (with sweep), 2 column FFT, 3 sample/chi2. */
-int gal_set_stage_timing(gal_ctx* ctx, int enable);
+/* Per-stage device timing.  Bit s of stage_mask enables stage s: each launch
+ * of an enabled stage is bracketed with CUDA events (two event records on the
+ * call's stream, so enable only the stages you need inside a timed loop).
+ * gal_stage_times synchronises and returns, per stage, the summed milliseconds
+ * and the number of timed launches since the mask was last set.
+ * Stages: 0 uv extent, 1 row FFT (with sweep), 2 column FFT, 3 sample/chi2.
+ * 0 disables timing; a mask outside [0, GAL_STAGE_ALL] is GAL_E_INVAL. */
+#define GAL_STAGE_ALL 0xF
+int gal_set_stage_timing(gal_ctx* ctx, int stage_mask);
 int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4);
 
 /* ---- observations ------------------------------------------------------------------- */
@@ -164,6 +168,29 @@ int gal_chi2_image_host_f32(gal_ctx* ctx, const float* image_host, int nxy, doub
 int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, double dxy,
                             double dRA, double dDec, double PA, const gal_data* data,
                             double* chi2_host, void* stream);
+
+/* ---- image sizing --------------------------------------------------------------------- */
+
+/* get_image_size (Sect. 3.3, criteria (i), (iia), (iib)): the image side *nxy_out
+ * (a power of two, possibly above the 8192 the transforms accept) and pixel
+ * size *dxy_out (radians) for the M points (u, v) (wavelengths, device memory).
+ * With rho_min / rho_max the shortest / longest baseline (finite points only):
+ *   (iia), PB == 0:  duv = rho_min / (Gamma f_min), Gamma = 0.6
+ *   (iib), PB > 0:   duv = min(1 / PB, rho_min / (Gamma f_min))   (PB: primary
+ *                    beam FWHM in radians; the field covers both the beam and
+ *                    f_min times the largest recoverable scale)
+ *   nxy = smallest power of two >= 2 f_max rho_max / duv   (criterion (i))
+ *   dxy = 1 / (nxy duv)
+ * f_min > 1 and f_max > 2 as the criteria require (the paper uses 5 and 2.5).
+ * Reads two doubles back: synchronises `stream`.  GAL_E_INVAL for M < 1, bad
+ * factors, PB < 0, or rho_min == 0 (a zero-length baseline) or no finite point;
+ * GAL_E_RANGE if nxy would exceed 2^62. */
+int gal_get_image_size_f32(gal_ctx* ctx, const float* u, const float* v, int64_t M, double PB,
+                           double f_min, double f_max, int64_t* nxy_out, double* dxy_out,
+                           void* stream);
+int gal_get_image_size_f64(gal_ctx* ctx, const double* u, const double* v, int64_t M, double PB,
+                           double f_min, double f_max, int64_t* nxy_out, double* dxy_out,
+                           void* stream);
 
 /* ---- allocation-free variant ---------------------------------------------------------- */
 

@@ -38,6 +38,7 @@ __all__ = [
     "half_spectrum",
     "rotate_uv",
     "uv_to_index",
+    "image_size",
     "bilinear",
     "sample_spectrum",
     "sample_image",
@@ -241,3 +242,45 @@ def uv_extent(u, v):
     if u.size == 0:
         return 0.0
     return float(np.sqrt(np.max(u * u + v * v)))
+
+
+# Largest-recoverable-scale constant of criterion (iia); the paper quotes
+# Gamma ~ 0.5 in general and 0.6 for ALMA.  Its matrix-size table is
+# reproduced with 0.6 only (0.5 gives 512 instead of 1024 for ALMA C43-3).
+MRS_GAMMA = 0.6
+
+
+def image_size(u, v, PB: float = 0.0, f_min: float = 5.0, f_max: float = 2.5):
+    """get_image_size of Sect. 3.3: (nxy, dxy) for the uv points.
+
+    Criterion (i): the modelled uv region must reach f_max times the longest
+    baseline, nxy * duv / 2 >= f_max * rho_max.  Criterion (iia): the field
+    nxy * dxy = 1 / duv must exceed f_min times the largest recoverable scale
+    Gamma / rho_min, i.e. duv = rho_min / (Gamma f_min).  Criterion (iib), when
+    the primary-beam FWHM PB (radians) is given: the field must also cover the
+    beam, duv <= 1 / PB.  nxy is the smallest power of two satisfying (i), and
+    dxy = 1 / (nxy duv).
+
+    Readings (the printed equations and the table disagree): the table's
+    N_lm (iia) column equals the power of two at or above
+    2 f_max Gamma f_min rho_max / rho_min, i.e. criteria (i) and (iia)
+    combined -- the printed N_lm equation drops f_max; its N_lm (iib) column
+    is reproduced when the field satisfies both (iia) and (iib) (the larger
+    of the two image sizes), and its pixel sizes equal 1 / (nxy duv).
+    """
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    r = np.sqrt(u * u + v * v)
+    r = r[np.isfinite(r)]
+    if r.size == 0 or not r.min() > 0.0:
+        raise ValueError("need at least one finite, non-zero baseline")
+    if not (f_min > 1.0 and f_max > 2.0 and PB >= 0.0):
+        raise ValueError("criteria need f_min > 1, f_max > 2, PB >= 0")
+    rho_min, rho_max = float(r.min()), float(r.max())
+    duv = rho_min / (MRS_GAMMA * f_min)           # (iia)
+    if PB > 0.0:
+        duv = min(duv, 1.0 / PB)                  # (iib)
+    need = 2.0 * f_max * rho_max / duv            # (i)
+    mant, expo = math.frexp(need)                 # need = mant * 2**expo, mant in [0.5, 1)
+    nxy = 2 ** (expo - 1) if mant == 0.5 else 2 ** expo
+    return int(nxy), 1.0 / (nxy * duv)

@@ -8,4 +8,4 @@ CUDA kernels behind a C ABI (include/galario_gb300.h).
     chi2 = ctx.chi2_image(image, dxy, obs, dRA, dDec, PA)
 """
 from .api import (Context, GalError, Observation, chi2_image, chi2_profile,  # noqa: F401
-                  default_context, sample_image, sample_profile, sweep)
+                  default_context, get_image_size, sample_image, sample_profile, sweep)

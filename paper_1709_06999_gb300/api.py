@@ -119,8 +119,13 @@ class Context:
     def launch_count(self) -> int:
         return int(self.lib.gal_launch_count(self.handle))
 
-    def set_stage_timing(self, enable: bool):
-        _check(self.handle, self.lib.gal_set_stage_timing(self.handle, int(enable)))
+    def set_stage_timing(self, enable=True, stages=None):
+        """Time every stage (enable=True), none (False), or only the stage
+        indices in `stages` (0 extent, 1 row FFT, 2 column FFT, 3 sample/chi2)."""
+        mask = 0xF if enable else 0
+        if enable and stages is not None:
+            mask = sum(1 << int(s) for s in set(stages))
+        _check(self.handle, self.lib.gal_set_stage_timing(self.handle, mask))
 
     def stage_times(self):
         """Per stage (extent, row FFT, column FFT, sample/chi2): (total ms, launches)."""
@@ -211,6 +216,20 @@ class Context:
                                obs.handle, ct.byref(res), self._stream()))
         return res.value
 
+    def get_image_size(self, u, v, PB: float = 0.0, f_min: float = 5.0, f_max: float = 2.5):
+        """(nxy, dxy) for the uv points (Sect. 3.3): criterion (iia) when PB == 0,
+        (iib) with PB the primary-beam FWHM in radians otherwise."""
+        u, v = self._dev(u), self._dev(v)
+        sfx = _suffix(u, v)
+        if u.numel() != v.numel():
+            raise ValueError("u and v must have the same length")
+        n = ct.c_int64()
+        d = ct.c_double()
+        fn = getattr(self.lib, f"gal_get_image_size_{sfx}")
+        _check(self.handle, fn(self.handle, u.data_ptr(), v.data_ptr(), u.numel(), PB, f_min,
+                               f_max, ct.byref(n), ct.byref(d), self._stream()))
+        return n.value, d.value
+
 
 _default: dict[int, Context] = {}
 
@@ -247,3 +266,7 @@ def chi2_profile(intensity, Rmin, dR, nxy, dxy, u, v, re, im, w, dRA=0.0, dDec=0
 
 def sweep(intensity, Rmin, dR, nxy, dxy, inc=0.0):
     return default_context(intensity.device.index).sweep(intensity, Rmin, dR, nxy, dxy, inc)
+
+
+def get_image_size(u, v, PB=0.0, f_min=5.0, f_max=2.5):
+    return default_context(u.device.index).get_image_size(u, v, PB, f_min, f_max)

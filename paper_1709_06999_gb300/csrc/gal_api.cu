@@ -45,6 +45,7 @@ struct gal_ctx {
   int partials_len = 0;
   unsigned* counter = nullptr;  // last-block-done counter (self-resetting)
   double* rho2 = nullptr;       // uv extent scratch for raw-pointer calls
+  double* uvrange = nullptr;    // min / max of u^2 + v^2 (image sizing)
   int* err = nullptr;           // index-check flag
   double* chi2_dev = nullptr;   // result slot for the host-buffer entry points
   void* stage_img = nullptr;    // image staging for the host-buffer entry points
@@ -55,7 +56,7 @@ struct gal_ctx {
   int smem_blocks[2] = {};         // chi2 gather blocks with a shared-memory window
   int aux_blocks = 0;
   uint64_t launches = 0;
-  bool timing = false;
+  int timing = 0;  // bit s: time stage s
   std::vector<TimedStage> timed;
   std::vector<cudaEvent_t> event_pool;
   double stage_ms[kStages] = {};
@@ -161,7 +162,8 @@ template <typename F> int stage(gal_ctx* ctx, int id, cudaStream_t st, F&& launc
   // drop a launch error left behind by an earlier, unrelated runtime call so
   // that the check after our launch reports our launch only
   (void)cudaGetLastError();
-  if (ctx->timing) {
+  const bool timed = (ctx->timing >> id) & 1;
+  if (timed) {
     if (ctx->timed.size() > 8192) harvest(ctx, 4096);
     a = pool_event(ctx);
     b = pool_event(ctx);
@@ -170,7 +172,7 @@ template <typename F> int stage(gal_ctx* ctx, int id, cudaStream_t st, F&& launc
   cudaError_t e = launch();
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   ctx->launches++;
-  if (ctx->timing) {
+  if (timed) {
     cudaEventRecord(b, st);
     ctx->timed.push_back({id, a, b});
   }
@@ -427,6 +429,35 @@ cudaError_t g_init_err = cudaSuccess;
 // ============================================================================
 // C ABI
 // ============================================================================
+template <typename T>
+int image_size_t(gal_ctx* ctx, const T* u, const T* v, int64_t M, double PB, double f_min,
+                 double f_max, int64_t* nxy_out, double* dxy_out, void* stream) {
+  if (!ctx || !u || !v || !nxy_out || !dxy_out || M < 1) return GAL_E_INVAL;
+  if (!aligned(u, sizeof(T)) || !aligned(v, sizeof(T))) return GAL_E_INVAL;
+  if (!(f_min > 1.0) || !(f_max > 2.0) || !std::isfinite(f_min) || !std::isfinite(f_max))
+    return GAL_E_INVAL;
+  if (!(PB >= 0.0) || !std::isfinite(PB)) return GAL_E_INVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GAL_TRY(stage(ctx, 0, st, [&] {
+    return gal::Launch<T>::uv_range(u, v, M, ctx->uvrange, ctx->aux_blocks, st);
+  }));
+  double r2[2];
+  GAL_CUDA(ctx, cudaMemcpyAsync(r2, ctx->uvrange, sizeof r2, cudaMemcpyDeviceToHost, st));
+  GAL_CUDA(ctx, cudaStreamSynchronize(st));
+  if (!(r2[0] > 0.0) || !(r2[1] >= r2[0]) || !std::isfinite(r2[1])) return GAL_E_INVAL;
+  const double rho_min = std::sqrt(r2[0]), rho_max = std::sqrt(r2[1]);
+  constexpr double kGamma = 0.6;  // ALMA's value of the MRS constant (Sect. 3.3)
+  double duv = rho_min / (kGamma * f_min);  // criterion (iia)
+  if (PB > 0.0 && 1.0 / PB < duv) duv = 1.0 / PB;  // criterion (iib)
+  const double need = 2.0 * f_max * rho_max / duv;  // criterion (i)
+  if (!(need <= 4.611686018427388e18)) return GAL_E_RANGE;  // 2^62
+  int64_t n = 1;
+  while ((double)n < need) n <<= 1;
+  *nxy_out = n;
+  *dxy_out = 1.0 / ((double)n * duv);
+  return GAL_OK;
+}
+
 extern "C" {
 
 const char* gal_strerror(int s) {
@@ -469,6 +500,7 @@ int gal_create(gal_ctx** out, int device) {
   if (!e) e = cudaMalloc(&ctx->partials, sizeof(double) * (size_t)maxb);
   if (!e) e = cudaMalloc(&ctx->counter, sizeof(unsigned));
   if (!e) e = cudaMalloc(&ctx->rho2, sizeof(double));
+  if (!e) e = cudaMalloc(&ctx->uvrange, 2 * sizeof(double));
   if (!e) e = cudaMalloc(&ctx->err, sizeof(int));
   if (!e) e = cudaMalloc(&ctx->chi2_dev, sizeof(double));
   if (!e) e = cudaMemset(ctx->counter, 0, sizeof(unsigned));
@@ -488,6 +520,7 @@ void gal_destroy(gal_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (void* p : {ctx->F1, ctx->Gw, (void*)ctx->partials, (void*)ctx->counter, (void*)ctx->rho2,
+                  (void*)ctx->uvrange,
                   (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img})
     if (p) cudaFree(p);
   for (auto& a : ctx->tw)
@@ -521,10 +554,10 @@ int gal_check(gal_ctx* ctx) {
 
 uint64_t gal_launch_count(const gal_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-int gal_set_stage_timing(gal_ctx* ctx, int enable) {
-  if (!ctx) return GAL_E_INVAL;
+int gal_set_stage_timing(gal_ctx* ctx, int stage_mask) {
+  if (!ctx || stage_mask < 0 || stage_mask > GAL_STAGE_ALL) return GAL_E_INVAL;
   harvest(ctx, 0);
-  ctx->timing = enable != 0;
+  ctx->timing = stage_mask;
   for (int s = 0; s < kStages; ++s) {
     ctx->stage_ms[s] = 0.0;
     ctx->stage_n[s] = 0;
@@ -540,6 +573,17 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4) {
     if (count_out4) count_out4[s] = ctx->stage_n[s];
   }
   return GAL_OK;
+}
+
+int gal_get_image_size_f32(gal_ctx* ctx, const float* u, const float* v, int64_t M, double PB,
+                           double f_min, double f_max, int64_t* nxy_out, double* dxy_out,
+                           void* stream) {
+  return image_size_t<float>(ctx, u, v, M, PB, f_min, f_max, nxy_out, dxy_out, stream);
+}
+int gal_get_image_size_f64(gal_ctx* ctx, const double* u, const double* v, int64_t M, double PB,
+                           double f_min, double f_max, int64_t* nxy_out, double* dxy_out,
+                           void* stream) {
+  return image_size_t<double>(ctx, u, v, M, PB, f_min, f_max, nxy_out, dxy_out, stream);
 }
 
 int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,

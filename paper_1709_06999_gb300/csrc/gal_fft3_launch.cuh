@@ -6,14 +6,18 @@
 
 namespace gal {
 
-// set a kernel's dynamic shared-memory limit once per process (one flag per
-// kernel: the template argument is the kernel itself)
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
+// the current device (the attribute is per device; set once per size).
 template <auto Kern> cudaError_t ensure_smem_attr(size_t smem) {
-  static size_t done = 0;
-  if (smem <= 48 * 1024 || done >= smem) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-  if (e == cudaSuccess) done = smem;
+  constexpr int kDev = 64;
+  static size_t done[kDev] = {};
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev >= 0 && dev < kDev && done[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kDev) done[dev] = smem;
   return e;
 }
 

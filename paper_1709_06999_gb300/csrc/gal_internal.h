@@ -41,6 +41,9 @@ template <typename T> struct Launch {
   static cudaError_t twiddles(void* tw, int N, cudaStream_t st);
   static cudaError_t extent(const T* u, const T* v, int64_t M, double* rho2, int blocks,
                             cudaStream_t st);
+  // range2[0] = min_k, range2[1] = max_k of u_k^2 + v_k^2 (finite points)
+  static cudaError_t uv_range(const T* u, const T* v, int64_t M, double* range2, int blocks,
+                              cudaStream_t st);
   static cudaError_t sweep(const T* I, const SweepParams& sp, int N, T* img, int blocks,
                            cudaStream_t st);
   // err: bit 2 is set if a staged copy's wait timed out (never expected)

@@ -71,6 +71,34 @@ __global__ void extent_kernel(const T* __restrict__ u, const T* __restrict__ v, 
   }
 }
 
+// min_k and max_k of u_k^2 + v_k^2 over the finite points (Sect. 3.3, criteria
+// (i) and (iia)); range2[0] must start at +inf and range2[1] at 0.  Non-negative
+// doubles order like their bit patterns, so the block results are combined
+// with integer atomics.
+template <typename T>
+__global__ void uv_range_kernel(const T* __restrict__ u, const T* __restrict__ v, int64_t M,
+                                double* __restrict__ range2) {
+  double lo = __longlong_as_double(0x7ff0000000000000ll), hi = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double a = (double)u[k], b = (double)v[k];
+    const double r = a * a + b * b;
+    if (r < lo) lo = r;  // NaN compares false both ways
+    if (r > hi && r < __longlong_as_double(0x7ff0000000000000ll)) hi = r;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double x = __shfl_down_sync(0xffffffffu, lo, o);
+    const double y = __shfl_down_sync(0xffffffffu, hi, o);
+    if (x < lo) lo = x;
+    if (y > hi) hi = y;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(reinterpret_cast<unsigned long long*>(range2), (unsigned long long)__double_as_longlong(lo));
+    atomicMax(reinterpret_cast<unsigned long long*>(range2 + 1), (unsigned long long)__double_as_longlong(hi));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // sweep: one pixel of the profile image (unshifted pixel (i, j)).
 // ---------------------------------------------------------------------------
@@ -150,7 +178,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
                                 cplx_t<T>* __restrict__ F1, const double* __restrict__ rho2,
                                 double S) {
   using C = cplx_t<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int M = N >> 1;
   const int Tg = M >= 8 ? M / 8 : 1;
@@ -202,7 +230,7 @@ __global__ void __launch_bounds__(1024)
 col_pass_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gp, int N,
                 const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S) {
   using C = cplx_t<T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const Bounds bd = block_bounds(rho2, S, N);
   const int Tg = N >= 8 ? N / 8 : 1;
@@ -1003,7 +1031,7 @@ gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __re
   const Window win = make_window(bd, p.N);
   typename Acc<T>::type acc;
   if constexpr (SMEM) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     C* sw = reinterpret_cast<C*>(smem_raw);
     const int nodes = bd.nrw * bd.Kc;
     if (nodes <= smem_nodes) {  // uniform over the grid; always true when sized by the host
@@ -1147,6 +1175,19 @@ cudaError_t Launch<T>::extent(const T* u, const T* v, int64_t M, double* rho2, i
   const int64_t need = (M + 255) / 256;
   const int grid = (int)(need < blocks ? need : blocks);
   extent_kernel<T><<<grid, 256, 0, st>>>(u, v, M, rho2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::uv_range(const T* u, const T* v, int64_t M, double* range2, int blocks,
+                                cudaStream_t st) {
+  const double init[2] = {std::numeric_limits<double>::infinity(), 0.0};
+  cudaError_t e = cudaMemcpyAsync(range2, init, sizeof init, cudaMemcpyHostToDevice, st);
+  if (e) return e;
+  if (M <= 0) return cudaSuccess;
+  const int64_t need = (M + 255) / 256;
+  const int grid = (int)(need < blocks ? need : blocks);
+  uv_range_kernel<T><<<grid, 256, 0, st>>>(u, v, M, range2);
   return cudaGetLastError();
 }
 

@@ -373,6 +373,27 @@ def check_sweep_pixels(O):
     assert abs(img[n // 2 - 6, n // 2] - (2.0 + 0.5 * (1.8 - Rmin)) * 0.09) < 1e-13
 
 
+def check_image_size_table(O):
+    """get_image_size against the paper's matrix-size table (Sect. 3.3):
+    N_lm of criteria (iia) and (iib) and the pixel size, for 14 ALMA and VLA
+    configurations (tests/golden/matrix_sizes.txt)."""
+    import os
+    arcsec = math.pi / 648000.0
+    lam = {"ALMA": 1.3e-3, "VLA": 7.0e-3}
+    dish = {"ALMA": 12.0, "VLA": 25.0}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "matrix_sizes.txt")
+    with open(path) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 14
+    for a, _, bmin, bmax, n1, n2, dth, _ in rows:
+        r = np.array([float(bmin), float(bmax)]) / lam[a]
+        u, v = r * np.cos([0.3, 2.0]), r * np.sin([0.3, 2.0])
+        n, dxy = O.image_size(u, v)
+        assert n == int(n1) and abs(dxy / arcsec - float(dth)) <= 0.0005 + 1e-9
+        n, _ = O.image_size(u, v, PB=1.5 * lam[a] / dish[a])
+        assert n == int(n2)
+
+
 ALL_CHECKS = [
     check_half_spectrum_bruteforce,
     check_sample_nodes_bruteforce,
@@ -389,4 +410,5 @@ ALL_CHECKS = [
     check_pa_quarter_turn,
     check_linearity,
     check_sweep_pixels,
+    check_image_size_table,
 ]

@@ -40,6 +40,12 @@ MUTANTS = {
     "sweep_no_centre": ("img[nxy // 2, nxy // 2] = centre * dxy * dxy", "pass"),
     "sweep_centre_not_extrapolated": ("centre = I[0] + slope * (0.0 - radii[0])", "centre = I[0]"),
     "pixel_origin_off_by_one": ("    half = nxy // 2\n    idx", "    half = nxy // 2 - 1\n    idx"),
+    "size_gamma_half": ("MRS_GAMMA = 0.6", "MRS_GAMMA = 0.5"),
+    "size_no_f_max": ("need = 2.0 * f_max * rho_max / duv", "need = 2.0 * rho_max / duv"),
+    "size_iib_alone": ("duv = min(duv, 1.0 / PB)", "duv = 1.0 / PB"),
+    "size_round_down": ("nxy = 2 ** (expo - 1) if mant == 0.5 else 2 ** expo", "nxy = 2 ** (expo - 1)"),
+    "size_pixel_from_extent": ("return int(nxy), 1.0 / (nxy * duv)",
+                               "return int(nxy), 1.0 / (2.0 * f_max * rho_max)"),
 }
 
 
