@@ -169,6 +169,61 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
                             double dRA, double dDec, double PA, const gal_data* data,
                             double* chi2_host, void* stream);
 
+/* ---- batches ------------------------------------------------------------------------- */
+
+/* One chi-square request of a batch: chi2Image when `image` is set, chi2Profile
+ * when `intensity` is set (exactly one of the two), with the arguments of
+ * gal_chi2_image_* / gal_chi2_profile_* (Sect. 2).  The arrays' precision is the
+ * observation's (`data`); nr, Rmin, dR and inc are read for profiles only. */
+typedef struct gal_request {
+  const void* image;      /* nxy*nxy values (device) or NULL */
+  const void* intensity;  /* nr values (device) or NULL */
+  int nr;
+  double Rmin, dR, inc;
+  int nxy;
+  double dxy, dRA, dDec, PA;
+  const gal_data* data;
+} gal_request;
+
+/* chi2_out[i] (device, n doubles) = the chi-square of request i: the many
+ * spectral channels or MCMC walkers of one fit in a few launches.  Requests of
+ * one precision and image side share each launch of the row FFT, of the column
+ * FFT and of the gather (up to 32 requests per launch; grid row = request), so
+ * the whole batch costs about three launches per distinct image side instead
+ * of three per request.  Every result is bitwise equal to the corresponding
+ * single call on the same context (same kernels, block partitions and
+ * reduction trees).  Requests the batched kernels do not cover (nxy < 32 in
+ * float32 / < 16 in float64, nxy above 8192 / 4096, images not 16-byte
+ * aligned) run as single calls inside the batch.
+ * Launch shapes: the first batch of each (precision, request count, largest
+ * side) is run once per candidate shape, timed with events on `stream`
+ * (synchronising it) and the fastest shape is kept for the context; results do
+ * not depend on the shape.  gal_set_batch_tuning(ctx, 0) turns this off
+ * (default shape).  The batch workspace (about nxy*Kc*2 complex values per
+ * request) grows on first use; like every call on a context, batches on
+ * different streams must not overlap.
+ * Errors: GAL_E_INVAL if any request is invalid (nothing is launched then). */
+int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, void* stream);
+int gal_set_batch_tuning(gal_ctx* ctx, int enable);
+
+/* A batch captured into a CUDA graph.  gal_chi2_batch_capture runs the batch
+ * once on `stream` (workspace, twiddles and launch-shape tuning happen there)
+ * and then records its launches into a graph, which gal_graph_launch replays
+ * on any stream.  The replay reads the requests' arrays (images, profiles,
+ * observations) as they are at replay time, so a fit that rewrites its model
+ * images in place relaunches the same graph; scalar arguments are those of the
+ * capture.  gal_graph_update re-records the batch with new requests of the
+ * same structure (same count, sides, kinds and observations) and updates the
+ * executable graph in place (GAL_E_INVAL if the structure changed).  A graph
+ * uses its context's batch workspace: keep the context alive, and do not run
+ * other batches on it while a replay may be in flight. */
+typedef struct gal_graph gal_graph;
+int gal_chi2_batch_capture(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out,
+                           void* stream, gal_graph** out);
+int gal_graph_update(gal_graph* g, const gal_request* reqs, int n, double* chi2_out);
+int gal_graph_launch(gal_graph* g, void* stream);
+void gal_graph_destroy(gal_graph* g);
+
 /* ---- image sizing --------------------------------------------------------------------- */
 
 /* get_image_size (Sect. 3.3, criteria (i), (iia), (iib)): the image side *nxy_out

@@ -42,6 +42,23 @@ for _p in ("f32", "f64"):
 
 _SIGNATURES["gal_chi2_image_noalloc_f32"] = (I32, [P, I32, D, D, D, D, P, P, P, P, P, I64, P, P])
 
+
+class GalRequest(ct.Structure):
+    """struct gal_request of include/galario_gb300.h."""
+    _fields_ = [("image", P), ("intensity", P), ("nr", I32), ("Rmin", D), ("dR", D),
+                ("inc", D), ("nxy", I32), ("dxy", D), ("dRA", D), ("dDec", D), ("PA", D),
+                ("data", P)]
+
+
+_SIGNATURES.update({
+    "gal_chi2_batch": (I32, [P, ct.POINTER(GalRequest), I32, P, P]),
+    "gal_set_batch_tuning": (I32, [P, I32]),
+    "gal_chi2_batch_capture": (I32, [P, ct.POINTER(GalRequest), I32, P, P, ct.POINTER(P)]),
+    "gal_graph_update": (I32, [P, ct.POINTER(GalRequest), I32, P]),
+    "gal_graph_launch": (I32, [P, P]),
+    "gal_graph_destroy": (None, [P]),
+})
+
 EXPORTED = sorted(_SIGNATURES)
 
 _lib = None

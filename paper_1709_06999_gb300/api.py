@@ -44,6 +44,88 @@ def _suffix(*tensors) -> str:
     return _SUFFIX[dt]
 
 
+class Request:
+    """One chi-square request of a batch: chi2Image (`image`) or chi2Profile
+    (`intensity` and its sweep arguments), against a registered Observation."""
+
+    def __init__(self, obs: "Observation", *, image=None, intensity=None, dxy: float,
+                 nxy: int | None = None, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
+                 Rmin: float = 0.0, dR: float = 0.0, inc: float = 0.0):
+        if (image is None) == (intensity is None):
+            raise ValueError("give exactly one of image and intensity")
+        self.obs, self.image, self.intensity = obs, image, intensity
+        if image is not None:
+            if image.dim() != 2 or image.shape[0] != image.shape[1]:
+                raise ValueError("image must be square")
+            nxy = image.shape[0]
+        elif nxy is None:
+            raise ValueError("a profile request needs nxy")
+        self.nxy, self.dxy, self.dRA, self.dDec, self.PA = int(nxy), dxy, dRA, dDec, PA
+        self.Rmin, self.dR, self.inc = Rmin, dR, inc
+
+    def _struct(self, ctx: "Context"):
+        dt = self.obs.dtype
+        if self.image is not None:
+            img = ctx._dev(self.image).contiguous()
+            if img.dtype != dt:
+                raise TypeError("image dtype must match the observation's")
+            keep = img
+            return _native.GalRequest(img.data_ptr(), None, 0, 0.0, 0.0, 0.0, self.nxy, self.dxy,
+                                      self.dRA, self.dDec, self.PA, self.obs.handle.value), keep
+        I = ctx._dev(self.intensity).contiguous()
+        if I.dtype != dt:
+            raise TypeError("intensity dtype must match the observation's")
+        return _native.GalRequest(None, I.data_ptr(), I.numel(), self.Rmin, self.dR, self.inc,
+                                  self.nxy, self.dxy, self.dRA, self.dDec, self.PA,
+                                  self.obs.handle.value), I
+
+
+def _request_array(ctx, requests):
+    structs, keep = [], []
+    for r in requests:
+        st, k = r._struct(ctx)
+        structs.append(st)
+        keep.append(k)
+    arr = (_native.GalRequest * max(1, len(structs)))(*structs)
+    return arr, keep
+
+
+class BatchGraph:
+    """A batch recorded into a CUDA graph (gal_chi2_batch_capture).  `out`
+    receives the chi-squares at every launch; the graph reads the requests'
+    tensors as they are when it runs."""
+
+    def __init__(self, ctx: "Context", requests, out):
+        self.ctx, self.out = ctx, out
+        arr, self._keep = _request_array(ctx, requests)
+        h = ct.c_void_p()
+        _check(ctx.handle, ctx.lib.gal_chi2_batch_capture(ctx.handle, arr, len(requests),
+                                                          out.data_ptr(), ctx._stream(),
+                                                          ct.byref(h)))
+        self.handle = h.value
+
+    def launch(self):
+        _check(self.ctx.handle, self.ctx.lib.gal_graph_launch(self.handle, self.ctx._stream()))
+        return self.out
+
+    def update(self, requests):
+        arr, keep = _request_array(self.ctx, requests)
+        _check(self.ctx.handle, self.ctx.lib.gal_graph_update(self.handle, arr, len(requests),
+                                                              self.out.data_ptr()))
+        self._keep = keep
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.gal_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Observation:
     """A registered set of M visibilities (u, v, Re, Im, w) resident on the device.
 
@@ -215,6 +297,26 @@ class Context:
         _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, dRA, dDec, PA,
                                obs.handle, ct.byref(res), self._stream()))
         return res.value
+
+    def chi2_batch(self, requests, out=None):
+        """chi-square of every Request, as a float64 tensor of len(requests)
+        (gal_chi2_batch: shared launches per pass and image side)."""
+        n = len(requests)
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=self.device)
+        arr, keep = _request_array(self, requests)
+        _check(self.handle, self.lib.gal_chi2_batch(self.handle, arr, n, out.data_ptr(),
+                                                    self._stream()))
+        del keep
+        return out
+
+    def set_batch_tuning(self, enable: bool):
+        _check(self.handle, self.lib.gal_set_batch_tuning(self.handle, int(enable)))
+
+    def capture_batch(self, requests, out=None) -> BatchGraph:
+        if out is None:
+            out = torch.empty(len(requests), dtype=torch.float64, device=self.device)
+        return BatchGraph(self, requests, out)
 
     def get_image_size(self, u, v, PB: float = 0.0, f_min: float = 5.0, f_max: float = 2.5):
         """(nxy, dxy) for the uv points (Sect. 3.3): criterion (iia) when PB == 0,

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cstring>
 #include <initializer_list>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -62,6 +64,14 @@ struct gal_ctx {
   double stage_ms[kStages] = {};
   int64_t stage_n[kStages] = {};
   char last_err[256] = {0};
+  // batches
+  void* batch_ws = nullptr;  // per-request spectra, windows and partial sums
+  size_t batch_ws_bytes = 0;
+  unsigned* batch_ctr = nullptr;  // per-request last-block counters, zero at rest
+  size_t batch_ctr_n = 0;
+  uint64_t ws_generation = 0;  // bumped whenever a workspace is reallocated
+  bool batch_tuning = true;
+  std::map<std::tuple<int, int, int>, gal::BatchShape> batch_shapes;
 };
 
 struct gal_data {
@@ -95,8 +105,11 @@ int log2i(int n) {
 }
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+uint64_t g_ws_generation = 0;  // every reallocation of any context's workspace
+
 cudaError_t grow(void** p, size_t* have, size_t need) {
   if (*have >= need) return cudaSuccess;
+  ++g_ws_generation;
   if (*p) {
     cudaError_t e = cudaFree(*p);
     if (e) return e;
@@ -265,6 +278,29 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   });
 }
 
+// Shape of the chi2 gather for a request with window `bd`: the window bytes to
+// stage in shared memory (0: read from L2) and the number of blocks.  Single
+// calls and batches use the same shape, so they reduce in the same order.
+template <typename T> int chi2_gather_shape(gal_ctx* ctx, const gal::Bounds& bd, size_t* wbytes_out) {
+  using C = gal::cplx_t<T>;
+  // Stage the kept spectrum window in shared memory when it is small enough
+  // (the pruned windows of long-baseline-free data usually are).
+  size_t wbytes = ((size_t)bd.nrw * bd.Kc * sizeof(C) + 15) & ~size_t(15);  // bulk-copy size
+  if (wbytes > (sizeof(T) == 4 ? kWindowSmemF32 : kWindowSmemF64)) wbytes = 0;
+  int blocks = ctx->gather_blocks[prec_index<T>()][1];
+  if (wbytes) {
+    if (wbytes != ctx->smem_blocks_key[prec_index<T>()]) {
+      ctx->smem_blocks_key[prec_index<T>()] = wbytes;
+      ctx->smem_blocks[prec_index<T>()] =
+          ctx->num_sms * gal::Launch<T>::gather_blocks_per_sm(true, wbytes);
+    }
+    blocks = ctx->smem_blocks[prec_index<T>()];
+  }
+  if (blocks > ctx->partials_len) blocks = ctx->partials_len;
+  *wbytes_out = wbytes;
+  return blocks;
+}
+
 template <typename T>
 int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
               double dxy, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
@@ -283,20 +319,8 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
       make_prefetch({d->u, d->v, d->re, d->im, d->w}, (size_t)d->M * sizeof(T));
   GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, bd.Kc, &pf, st));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
-  // Stage the kept spectrum window in shared memory when it is small enough
-  // (the pruned windows of long-baseline-free data usually are).
-  size_t wbytes = ((size_t)bd.nrw * bd.Kc * sizeof(C) + 15) & ~size_t(15);  // bulk-copy size
-  if (wbytes > (sizeof(T) == 4 ? kWindowSmemF32 : kWindowSmemF64)) wbytes = 0;
-  int blocks = ctx->gather_blocks[prec_index<T>()][1];
-  if (wbytes) {
-    if (wbytes != ctx->smem_blocks_key[prec_index<T>()]) {
-      ctx->smem_blocks_key[prec_index<T>()] = wbytes;
-      ctx->smem_blocks[prec_index<T>()] =
-          ctx->num_sms * gal::Launch<T>::gather_blocks_per_sm(true, wbytes);
-    }
-    blocks = ctx->smem_blocks[prec_index<T>()];
-  }
-  if (blocks > ctx->partials_len) blocks = ctx->partials_len;
+  size_t wbytes;
+  const int blocks = chi2_gather_shape<T>(ctx, bd, &wbytes);
   return stage(ctx, 3, st, [&] {
     return gal::Launch<T>::gather(ctx->Gw, gp, d->rho2, static_cast<const T*>(d->u),
                                   static_cast<const T*>(d->v), static_cast<const T*>(d->re),
@@ -458,6 +482,326 @@ int image_size_t(gal_ctx* ctx, const T* u, const T* v, int64_t M, double PB, dou
   return GAL_OK;
 }
 
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+  std::vector<gal::BatchItem> items[2];  // per precision (0 float, 1 double)
+  std::vector<int> single;               // requests run as single calls
+  std::vector<int> empty;                // requests with M == 0
+  int max_nxy[2] = {0, 0};
+};
+
+int check_request(gal_ctx* ctx, const gal_request& r) {
+  const gal_data* d = r.data;
+  if (!d || d->ctx != ctx) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(r.nxy, r.dxy));
+  if (!std::isfinite(r.dRA) || !std::isfinite(r.dDec) || !std::isfinite(r.PA)) return GAL_E_INVAL;
+  const size_t rb = (size_t)d->real_bytes;
+  if ((r.image != nullptr) == (r.intensity != nullptr)) return GAL_E_INVAL;
+  if (r.image) {
+    if (!aligned(r.image, 2 * rb)) return GAL_E_INVAL;
+  } else {
+    GAL_TRY(check_profile(r.intensity, r.nr, r.Rmin, r.dR, r.inc));
+    if (!aligned(r.intensity, rb)) return GAL_E_INVAL;
+  }
+  return GAL_OK;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+bool batchable(const gal_request& r) {
+  return gal::BatchLaunch<T>::supported(r.nxy) && (!r.image || aligned(r.image, 16));
+}
+
+// Validate every request, sort them into batched / single / empty, and lay
+// out (growing if needed) the batch workspace.
+int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, BatchPlan& pl) {
+  for (int i = 0; i < n; ++i) GAL_TRY(check_request(ctx, reqs[i]));
+  size_t bytes = 0;
+  size_t nctr = 0;
+  struct Off {
+    size_t f1, gw, part;
+  };
+  std::vector<Off> offs[2];
+  for (int i = 0; i < n; ++i) {
+    const gal_request& r = reqs[i];
+    const gal_data* d = r.data;
+    const int p = d->real_bytes == 8 ? 1 : 0;
+    if (d->M == 0) {
+      pl.empty.push_back(i);
+      continue;
+    }
+    const bool ok = p ? batchable<double>(r) : batchable<float>(r);
+    if (!ok) {
+      pl.single.push_back(i);
+      continue;
+    }
+    gal::BatchItem b{};
+    b.image = r.image;
+    b.I = r.intensity;
+    b.sp = gal::SweepParams{r.Rmin, r.dR, r.dxy, r.inc, r.nr};
+    b.N = r.nxy;
+    b.S = (double)r.nxy * r.dxy;
+    b.rho2 = d->rho2;
+    const gal::Bounds bd = gal::make_bounds(d->rho2_host, b.S, r.nxy);
+    b.Kc = bd.Kc;
+    b.nrw = bd.nrw;
+    b.gp = gather_params(r.nxy, r.dxy, r.dRA, r.dDec, r.PA);
+    b.u = d->u;
+    b.v = d->v;
+    b.re = d->re;
+    b.im = d->im;
+    b.w = d->w;
+    b.M = d->M;
+    b.chi2_out = chi2_out + i;
+    b.edge = bd.r0 == 0;
+    b.grid = p ? chi2_gather_shape<double>(ctx, bd, &b.wbytes)
+               : chi2_gather_shape<float>(ctx, bd, &b.wbytes);
+    const size_t cb = 2 * (size_t)d->real_bytes;  // complex value
+    Off o;
+    o.f1 = bytes;
+    bytes = round_up(bytes + (size_t)r.nxy * bd.Kc * cb, 256);
+    o.gw = bytes;
+    bytes = round_up(bytes + round_up((size_t)bd.nrw * bd.Kc * cb, 16) + 16, 256);
+    o.part = bytes;
+    bytes = round_up(bytes + sizeof(double) * (size_t)b.grid, 256);
+    b.counter = reinterpret_cast<unsigned*>(nctr);  // index, resolved below
+    ++nctr;
+    pl.items[p].push_back(b);
+    offs[p].push_back(o);
+    pl.max_nxy[p] = std::max(pl.max_nxy[p], r.nxy);
+  }
+  GAL_CUDA(ctx, grow(&ctx->batch_ws, &ctx->batch_ws_bytes, bytes));
+  if (nctr > ctx->batch_ctr_n) {
+    size_t have = ctx->batch_ctr_n * sizeof(unsigned);
+    GAL_CUDA(ctx, grow(reinterpret_cast<void**>(&ctx->batch_ctr), &have, nctr * sizeof(unsigned)));
+    GAL_CUDA(ctx, cudaMemset(ctx->batch_ctr, 0, nctr * sizeof(unsigned)));
+    ctx->batch_ctr_n = nctr;
+  }
+  char* base = static_cast<char*>(ctx->batch_ws);
+  for (int p = 0; p < 2; ++p)
+    for (size_t k = 0; k < pl.items[p].size(); ++k) {
+      gal::BatchItem& b = pl.items[p][k];
+      b.F1 = base + offs[p][k].f1;
+      b.Gw = base + offs[p][k].gw;
+      b.partials = reinterpret_cast<double*>(base + offs[p][k].part);
+      b.counter = ctx->batch_ctr + reinterpret_cast<size_t>(b.counter);
+    }
+  return GAL_OK;
+}
+
+template <typename T> int ensure_twiddles(gal_ctx* ctx, int nxy) {
+  using C = gal::cplx_t<T>;
+  void*& tw = ctx->tw[prec_index<T>()][log2i(nxy)];
+  if (!tw) {
+    GAL_CUDA(ctx, cudaMalloc(&tw, (size_t)nxy * sizeof(C)));
+    ++g_ws_generation;
+    GAL_CUDA(ctx, gal::Launch<T>::twiddles(tw, nxy, 0));
+    GAL_CUDA(ctx, cudaStreamSynchronize(0));
+    ctx->launches++;
+  }
+  return GAL_OK;
+}
+
+// Enqueue the batched passes of one precision with launch shape `sh`.
+template <typename T>
+int enqueue_items(gal_ctx* ctx, const std::vector<gal::BatchItem>& items,
+                  const gal::BatchShape& sh, cudaStream_t st) {
+  if (items.empty()) return GAL_OK;
+  const void* const* tw = ctx->tw[prec_index<T>()];
+  const int n = (int)items.size();
+  int nl = 0;
+  GAL_TRY(stage(ctx, 1, st, [&] {
+    return gal::BatchLaunch<T>::rows(items.data(), n, tw, ctx->err, sh, &nl, st);
+  }));
+  ctx->launches += nl - 1;
+  nl = 0;
+  GAL_TRY(stage(ctx, 2, st, [&] {
+    return gal::BatchLaunch<T>::cols(items.data(), n, tw, sh, &nl, st);
+  }));
+  ctx->launches += nl - 1;
+  nl = 0;
+  GAL_TRY(stage(ctx, 3, st, [&] {
+    return gal::BatchLaunch<T>::gather(items.data(), n, sh, &nl, st);
+  }));
+  ctx->launches += nl - 1;
+  return GAL_OK;
+}
+
+constexpr gal::BatchShape kDefaultShape{1, gal::kBatchJobs};
+
+// Everything of a planned batch except the batched passes' shapes.
+int enqueue_rest(gal_ctx* ctx, const gal_request* reqs, const BatchPlan& pl, double* chi2_out,
+                 cudaStream_t st) {
+  for (int i : pl.empty) GAL_CUDA(ctx, cudaMemsetAsync(chi2_out + i, 0, sizeof(double), st));
+  for (int i : pl.single) {
+    const gal_request& r = reqs[i];
+    const gal::SweepParams sp{r.Rmin, r.dR, r.dxy, r.inc, r.nr};
+    if (r.data->real_bytes == 8)
+      GAL_TRY(chi2_impl<double>(ctx, static_cast<const double*>(r.image),
+                                static_cast<const double*>(r.intensity), sp, r.nxy, r.dxy, r.dRA,
+                                r.dDec, r.PA, r.data, chi2_out + i, st));
+    else
+      GAL_TRY(chi2_impl<float>(ctx, static_cast<const float*>(r.image),
+                               static_cast<const float*>(r.intensity), sp, r.nxy, r.dxy, r.dRA,
+                               r.dDec, r.PA, r.data, chi2_out + i, st));
+  }
+  return GAL_OK;
+}
+
+// Launch shape for precision p of this plan: cached, or tuned now by timing
+// every candidate on the stream (results are identical for all of them).
+int batch_shape(gal_ctx* ctx, const BatchPlan& pl, int p, cudaStream_t st, gal::BatchShape* out) {
+  *out = kDefaultShape;
+  const int n = (int)pl.items[p].size();
+  if (n == 0) return GAL_OK;
+  const auto key = std::make_tuple(p, n, pl.max_nxy[p]);
+  auto it = ctx->batch_shapes.find(key);
+  if (it != ctx->batch_shapes.end()) {
+    *out = it->second;
+    return GAL_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GAL_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
+  if (!ctx->batch_tuning || cap != cudaStreamCaptureStatusNone) return GAL_OK;
+  const gal::BatchShape cands[] = {{1, 32}, {2, 32}, {4, 32}, {1, 8}, {2, 8}, {4, 16}};
+  cudaEvent_t a, b;
+  GAL_CUDA(ctx, cudaEventCreate(&a));
+  GAL_CUDA(ctx, cudaEventCreate(&b));
+  float best = 1e30f;
+  gal::BatchShape pick = kDefaultShape;
+  const int saved_timing = ctx->timing;
+  ctx->timing = 0;
+  int status = GAL_OK;
+  for (const auto& c : cands) {
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && status == GAL_OK; ++rep) {  // first run warms up
+      cudaEventRecord(a, st);
+      status = p ? enqueue_items<double>(ctx, pl.items[1], c, st)
+                 : enqueue_items<float>(ctx, pl.items[0], c, st);
+      cudaEventRecord(b, st);
+      if (status == GAL_OK && cudaEventSynchronize(b) == cudaSuccess) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, a, b);
+        ms = std::min(ms, t);
+      }
+    }
+    if (status != GAL_OK) break;
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  ctx->timing = saved_timing;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (status != GAL_OK) return status;
+  ctx->batch_shapes[key] = pick;
+  *out = pick;
+  return GAL_OK;
+}
+
+int run_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, cudaStream_t st,
+              bool allow_setup) {
+  BatchPlan pl;
+  GAL_TRY(plan_batch(ctx, reqs, n, chi2_out, pl));
+  if (allow_setup) {
+    for (const auto& b : pl.items[0]) GAL_TRY(ensure_twiddles<float>(ctx, b.N));
+    for (const auto& b : pl.items[1]) GAL_TRY(ensure_twiddles<double>(ctx, b.N));
+  }
+  gal::BatchShape sh[2];
+  for (int p = 0; p < 2; ++p) GAL_TRY(batch_shape(ctx, pl, p, st, &sh[p]));
+  GAL_TRY(enqueue_items<float>(ctx, pl.items[0], sh[0], st));
+  GAL_TRY(enqueue_items<double>(ctx, pl.items[1], sh[1], st));
+  return enqueue_rest(ctx, reqs, pl, chi2_out, st);
+}
+
+}  // namespace
+
+struct gal_graph {
+  gal_ctx* ctx = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<gal_request> reqs;
+  double* chi2_out = nullptr;
+  uint64_t generation = 0;  // workspace generation the graph was recorded against
+  uint64_t launches = 0;    // kernels per replay
+};
+
+namespace {
+
+// Record the batch into a new graph (nothing runs).  The workspace and
+// twiddles must already exist (a preceding run_batch on the same requests).
+int record_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, cudaGraph_t* g,
+                 uint64_t* launches) {
+  cudaStream_t cs;
+  GAL_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const int saved_timing = ctx->timing;
+  ctx->timing = 0;
+  const uint64_t l0 = ctx->launches;
+  const uint64_t gen0 = g_ws_generation;
+  int s = GAL_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    s = run_batch(ctx, reqs, n, chi2_out, cs, false);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (s == GAL_OK && e == cudaSuccess && g_ws_generation != gen0) s = GAL_E_INVAL;
+    if (s == GAL_OK && e == cudaSuccess) {
+      *g = graph;
+    } else if (graph) {
+      cudaGraphDestroy(graph);
+    }
+  }
+  *launches = ctx->launches - l0;
+  ctx->launches = l0;
+  ctx->timing = saved_timing;
+  cudaStreamDestroy(cs);
+  if (s != GAL_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  return GAL_OK;
+}
+
+bool same_structure(const std::vector<gal_request>& a, const gal_request* b, int n) {
+  if ((int)a.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (a[i].data != b[i].data || a[i].nxy != b[i].nxy ||
+        (a[i].image == nullptr) != (b[i].image == nullptr))
+      return false;
+  return true;
+}
+
+int graph_record_into(gal_graph* gr, const gal_request* reqs, int n, double* chi2_out) {
+  gal_ctx* ctx = gr->ctx;
+  cudaGraph_t g = nullptr;
+  uint64_t nl = 0;
+  GAL_TRY(record_batch(ctx, reqs, n, chi2_out, &g, &nl));
+  cudaError_t e = cudaSuccess;
+  if (gr->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    e = cudaGraphExecUpdate(gr->exec, g, &info);
+    if (e != cudaSuccess) {  // topology changed: instantiate afresh
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(gr->exec);
+      gr->exec = nullptr;
+    }
+  }
+  if (!gr->exec) e = cudaGraphInstantiate(&gr->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  gr->reqs.assign(reqs, reqs + n);
+  gr->chi2_out = chi2_out;
+  gr->generation = g_ws_generation;
+  gr->launches = nl;
+  return GAL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* gal_strerror(int s) {
@@ -520,7 +864,7 @@ void gal_destroy(gal_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (void* p : {ctx->F1, ctx->Gw, (void*)ctx->partials, (void*)ctx->counter, (void*)ctx->rho2,
-                  (void*)ctx->uvrange,
+                  (void*)ctx->uvrange, ctx->batch_ws, (void*)ctx->batch_ctr,
                   (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img})
     if (p) cudaFree(p);
   for (auto& a : ctx->tw)
@@ -573,6 +917,79 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4) {
     if (count_out4) count_out4[s] = ctx->stage_n[s];
   }
   return GAL_OK;
+}
+
+int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!reqs || !chi2_out))) return GAL_E_INVAL;
+  if (n == 0) return GAL_OK;
+  if (!aligned(chi2_out, sizeof(double))) return GAL_E_INVAL;
+  return run_batch(ctx, reqs, n, chi2_out, static_cast<cudaStream_t>(stream), true);
+}
+
+int gal_set_batch_tuning(gal_ctx* ctx, int enable) {
+  if (!ctx) return GAL_E_INVAL;
+  ctx->batch_tuning = enable != 0;
+  return GAL_OK;
+}
+
+int gal_chi2_batch_capture(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out,
+                           void* stream, gal_graph** out) {
+  if (!out) return GAL_E_INVAL;
+  *out = nullptr;
+  if (!ctx || n < 1 || !reqs || !chi2_out || !aligned(chi2_out, sizeof(double)))
+    return GAL_E_INVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // one ordinary run: workspace, twiddles and launch shapes are set up here
+  GAL_TRY(run_batch(ctx, reqs, n, chi2_out, st, true));
+  GAL_CUDA(ctx, cudaStreamSynchronize(st));
+  gal_graph* g = new (std::nothrow) gal_graph;
+  if (!g) return GAL_E_NOMEM;
+  g->ctx = ctx;
+  const int s = graph_record_into(g, reqs, n, chi2_out);
+  if (s != GAL_OK) {
+    gal_graph_destroy(g);
+    return s;
+  }
+  *out = g;
+  return GAL_OK;
+}
+
+int gal_graph_update(gal_graph* g, const gal_request* reqs, int n, double* chi2_out) {
+  if (!g || !reqs || !chi2_out || !aligned(chi2_out, sizeof(double))) return GAL_E_INVAL;
+  if (!same_structure(g->reqs, reqs, n)) return GAL_E_INVAL;
+  for (int i = 0; i < n; ++i) GAL_TRY(check_request(g->ctx, reqs[i]));
+  return graph_record_into(g, reqs, n, chi2_out);
+}
+
+int gal_graph_launch(gal_graph* g, void* stream) {
+  if (!g || !g->exec) return GAL_E_INVAL;
+  gal_ctx* ctx = g->ctx;
+  if (g->generation != g_ws_generation) {
+    // a workspace the graph points into was reallocated since it was recorded:
+    // set the batch up again (allocations happen here, outside any capture)
+    // and re-record it
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BatchPlan pl;
+    GAL_TRY(plan_batch(ctx, g->reqs.data(), (int)g->reqs.size(), g->chi2_out, pl));
+    for (const auto& b : pl.items[0]) GAL_TRY(ensure_twiddles<float>(ctx, b.N));
+    for (const auto& b : pl.items[1]) GAL_TRY(ensure_twiddles<double>(ctx, b.N));
+    for (int i : pl.single) {
+      const gal_request& r = g->reqs[i];
+      GAL_TRY(r.data->real_bytes == 8 ? ensure<double>(ctx, r.nxy) : ensure<float>(ctx, r.nxy));
+    }
+    GAL_CUDA(ctx, cudaStreamSynchronize(st));
+    const std::vector<gal_request> reqs = g->reqs;
+    GAL_TRY(graph_record_into(g, reqs.data(), (int)reqs.size(), g->chi2_out));
+  }
+  GAL_CUDA(ctx, cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  ctx->launches += g->launches;
+  return GAL_OK;
+}
+
+void gal_graph_destroy(gal_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
 }
 
 int gal_get_image_size_f32(gal_ctx* ctx, const float* u, const float* v, int64_t M, double PB,

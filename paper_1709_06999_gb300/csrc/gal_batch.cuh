@@ -1,0 +1,223 @@
+// Batched passes: the row FFT, the column FFT and the gather/chi-square of
+// many requests, one launch per pass, transform length and chunk of at most
+// kBatchJobs requests.  Grid row y of a launch is request y of the chunk; its
+// arguments come from the launch's __grid_constant__ job array.  Each request
+// is computed by the same code and, for the gather, with the same block
+// partition and reduction tree as a single call, so batched and single-call
+// results are bitwise equal.
+#pragma once
+
+#include <type_traits>
+#include <vector>
+
+#include "gal_fft3_launch.cuh"
+
+namespace gal {
+
+template <typename T> bool BatchLaunch<T>::supported(int N) {
+  const int lg = ilog2i(N);
+  return (1 << lg) == N && N / 2 >= FftV<T>::V && lg - 1 <= 12 && lg <= col3_max_lg<T>();
+}
+
+namespace batch {
+
+inline int chunk_of(const BatchShape& sh) {
+  int k = sh.jobs_per_launch;
+  return k < 1 ? 1 : (k > kBatchJobs ? kBatchJobs : k);
+}
+
+// rows: the chunk `idx[0..n)` of items, all of length 2^(LG+1), all swept
+// (SWEEP) or all images
+template <typename T, int LG, bool SWEEP>
+cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int* err,
+                 const BatchShape& sh, cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int M = 1 << LG, N = 2 * M;
+  using SH = Shape3<T, M, N>;
+  Jobs<RowJob<T>, kBatchJobs> jb{};
+  for (int k = 0; k < n; ++k) {
+    const BatchItem& b = it[idx[k]];
+    jb.j[k] = RowJob<T>{static_cast<const T*>(b.image), static_cast<const T*>(b.I),
+                        SWEEP ? sweep_cast<T>(b.sp) : SweepT<T>{}, static_cast<C*>(b.F1), b.rho2,
+                        b.S};
+  }
+  const C* twc = static_cast<const C*>(tw);
+  if constexpr (!SWEEP) {
+    constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs>;
+    const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
+    cudaError_t e = ensure_smem_attr<kern>(smem);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+    if (e) return e;
+    if (per_sm < 1) per_sm = 1;
+    // persistent blocks per request: the GPU's resident blocks (times the
+    // shape's factor) shared by the chunk's requests
+    int x = (per_sm * current_device_sms() * (sh.row_blocks < 1 ? 1 : sh.row_blocks) + n - 1) / n;
+    if (x > N / SH::G) x = N / SH::G;
+    if (x < 1) x = 1;
+    kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, twc, err);
+  } else {
+    constexpr auto kern = row_fft3_kernel<T, LG, false, true, kBatchJobs>;
+    const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
+    const cudaError_t e = ensure_smem_attr<kern>(smem);
+    if (e) return e;
+    kern<<<dim3(N / SH::G, n), SH::threads, smem, st>>>(jb, twc, err);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int LG>
+cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int N = 1 << LG;
+  using SH = Shape3<T, N, (1 << 30)>;
+  constexpr auto kern = col_fft3_kernel<T, LG, kBatchJobs>;
+  const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
+  const cudaError_t e = ensure_smem_attr<kern>(smem);
+  if (e) return e;
+  Jobs<ColJob<T>, kBatchJobs> jb{};
+  int kc = 1;
+  for (int k = 0; k < n; ++k) {
+    const BatchItem& b = it[idx[k]];
+    jb.j[k] = ColJob<T>{static_cast<const C*>(b.F1), static_cast<C*>(b.Gw), b.rho2, b.S};
+    kc = b.Kc > kc ? b.Kc : kc;
+  }
+  int x = (kc + SH::G - 1) / SH::G;
+  const int cap = 2 * current_device_sms();
+  if (x > cap) x = cap;
+  kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, static_cast<const C*>(tw), x, L2Prefetch{});
+  return cudaGetLastError();
+}
+
+template <typename T, bool SMEM, bool EDGE>
+cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStream_t st) {
+  using C = cplx_t<T>;
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  Jobs<GatherJob<T>, kBatchJobs> jb{};
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const BatchItem& b = it[idx[k]];
+    const int vec = al16(b.u) && al16(b.v) && al16(b.re) && al16(b.im) && al16(b.w);
+    jb.j[k] = GatherJob<T>{static_cast<const C*>(b.Gw), GatherT<T>::make(b.gp), b.rho2,
+                           static_cast<const T*>(b.u), static_cast<const T*>(b.v),
+                           static_cast<const T*>(b.re), static_cast<const T*>(b.im),
+                           static_cast<const T*>(b.w), b.M, vec, nullptr, b.partials,
+                           b.counter, b.chi2_out};
+    smem = b.wbytes > smem ? b.wbytes : smem;
+  }
+  if (!SMEM) smem = 0;
+  constexpr auto kern = gather_kernel<T, true, SMEM, EDGE, kBatchJobs>;
+  const cudaError_t e = ensure_smem_attr<kern>(smem);
+  if (e) return e;
+  const int threads = gather_threads<SMEM>();
+  kern<<<dim3(grid, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)));
+  return cudaGetLastError();
+}
+
+// length dispatch
+template <typename T, int LG, typename F> cudaError_t by_lg(int lg, F&& f) {
+  if constexpr (LG > 13) {
+    return cudaErrorNotSupported;
+  } else {
+    if (lg == LG) return f(std::integral_constant<int, LG>{});
+    return by_lg<T, LG + 1>(lg, f);
+  }
+}
+
+// apply f(chunk indices, count) over the items selected by `pick`, grouped by
+// key(item) and chunked
+template <typename Key, typename Pick, typename F>
+cudaError_t for_chunks(const BatchItem* it, int n, const BatchShape& sh, Pick&& pick, Key&& key,
+                       F&& f) {
+  const int cap = chunk_of(sh);
+  std::vector<char> done(n, 0);
+  std::vector<int> idx;
+  idx.reserve(cap);
+  for (int a = 0; a < n; ++a) {
+    if (done[a] || !pick(it[a])) continue;
+    const auto ka = key(it[a]);
+    idx.clear();
+    for (int b = a; b < n; ++b) {
+      if (done[b] || !pick(it[b]) || !(key(it[b]) == ka)) continue;
+      done[b] = 1;
+      idx.push_back(b);
+      if ((int)idx.size() == cap) {
+        const cudaError_t e = f(idx.data(), (int)idx.size(), it[idx[0]]);
+        if (e) return e;
+        idx.clear();
+      }
+    }
+    if (!idx.empty()) {
+      const cudaError_t e = f(idx.data(), (int)idx.size(), it[idx[0]]);
+      if (e) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace batch
+
+template <typename T>
+cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* tw, int* err,
+                                 const BatchShape& sh, int* launches, cudaStream_t st) {
+  auto pick = [](const BatchItem&) { return true; };
+  auto key = [](const BatchItem& b) { return b.N * 2 + (b.I ? 1 : 0); };
+  return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
+    const int lg = ilog2i(b0.N);
+    const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg - 1, [&](auto L) {
+      constexpr int LG = decltype(L)::value;
+      if constexpr (LG > 12) {
+        return cudaErrorNotSupported;
+      } else {
+        return b0.I ? batch::rows<T, LG, true>(it, idx, m, tw[lg], err, sh, st)
+                    : batch::rows<T, LG, false>(it, idx, m, tw[lg], err, sh, st);
+      }
+    });
+    if (!e) ++*launches;
+    return e;
+  });
+}
+
+template <typename T>
+cudaError_t BatchLaunch<T>::cols(const BatchItem* it, int n, const void* const* tw,
+                                 const BatchShape& sh, int* launches, cudaStream_t st) {
+  auto pick = [](const BatchItem&) { return true; };
+  auto key = [](const BatchItem& b) { return b.N; };
+  return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
+    const int lg = ilog2i(b0.N);
+    const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg, [&](auto L) {
+      constexpr int LG = decltype(L)::value;
+      if constexpr (LG > col3_max_lg<T>()) {
+        return cudaErrorNotSupported;
+      } else {
+        return batch::cols<T, LG>(it, idx, m, tw[lg], st);
+      }
+    });
+    if (!e) ++*launches;
+    return e;
+  });
+}
+
+template <typename T>
+cudaError_t BatchLaunch<T>::gather(const BatchItem* it, int n, const BatchShape& sh,
+                                   int* launches, cudaStream_t st) {
+  auto pick = [](const BatchItem&) { return true; };
+  // one launch shape per chunk: variant and blocks per request
+  auto key = [](const BatchItem& b) {
+    return (int64_t)b.grid * 4 + (b.wbytes ? 2 : 0) + (b.edge ? 1 : 0);
+  };
+  return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
+    cudaError_t e;
+    if (b0.wbytes)
+      e = b0.edge ? batch::gather<T, true, true>(it, idx, m, b0.grid, st)
+                  : batch::gather<T, true, false>(it, idx, m, b0.grid, st);
+    else
+      e = b0.edge ? batch::gather<T, false, true>(it, idx, m, b0.grid, st)
+                  : batch::gather<T, false, false>(it, idx, m, b0.grid, st);
+    if (!e) ++*launches;
+    return e;
+  });
+}
+
+}  // namespace gal

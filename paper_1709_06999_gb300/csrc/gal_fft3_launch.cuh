@@ -29,8 +29,10 @@ cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const
   using SH = Shape3<T, M, N>;
   const C* twc = static_cast<const C*>(tw);
   C* out = static_cast<C*>(F1);
+  Jobs<RowJob<T>, 1> jb;
+  jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, out, rho2, S};
   if constexpr (!SWEEP) {
-    constexpr auto kern = row_fft3_kernel<T, LG, true, false>;
+    constexpr auto kern = row_fft3_kernel<T, LG, true, false, 1>;
     const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
     cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
@@ -40,14 +42,13 @@ cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const
     if (per_sm < 1) per_sm = 1;
     int grid = per_sm * current_device_sms();
     if (grid > N / SH::G) grid = N / SH::G;
-    kern<<<grid, SH::threads, smem, st>>>(image, nullptr, SweepT<T>{}, twc, out, rho2, S, err);
+    kern<<<grid, SH::threads, smem, st>>>(jb, twc, err);
   } else {
-    constexpr auto kern = row_fft3_kernel<T, LG, false, true>;
+    constexpr auto kern = row_fft3_kernel<T, LG, false, true, 1>;
     const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
     const cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
-    kern<<<N / SH::G, SH::threads, smem, st>>>(nullptr, I, sweep_cast<T>(sp), twc, out, rho2, S,
-                                               err);
+    kern<<<N / SH::G, SH::threads, smem, st>>>(jb, twc, err);
   }
   return cudaGetLastError();
 }
@@ -58,7 +59,7 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
-  constexpr auto kern = col_fft3_kernel<T, LG>;
+  constexpr auto kern = col_fft3_kernel<T, LG, 1>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -70,9 +71,9 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
   L2Prefetch none{};
   const L2Prefetch& p = pf ? *pf : none;
   const int pf_blocks = p.n > 0 ? 16 : 0;
-  kern<<<col_blocks + pf_blocks, SH::threads, smem, st>>>(static_cast<const C*>(F1),
-                                                          static_cast<C*>(Gw),
-                                                          static_cast<const C*>(tw), rho2, S,
+  Jobs<ColJob<T>, 1> jb;
+  jb.j[0] = ColJob<T>{static_cast<const C*>(F1), static_cast<C*>(Gw), rho2, S};
+  kern<<<col_blocks + pf_blocks, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw),
                                                           col_blocks, p);
   return cudaGetLastError();
 }

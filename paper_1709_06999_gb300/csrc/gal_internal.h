@@ -62,6 +62,54 @@ template <typename T> struct Launch {
                             cudaStream_t st);
 };
 
+// Requests per launch of the batched passes (their job arrays are kernel
+// parameters: 32 gather jobs take about 8 KB of the 32 KB parameter space).
+constexpr int kBatchJobs = 32;
+
+// One request of a batch, planned by the C-ABI layer (host values and device
+// pointers).  Exactly one of image / I is set.
+struct BatchItem {
+  const void* image;   // nxy x nxy image, 16-byte aligned
+  const void* I;       // radial profile (the sweep runs inside the row pass)
+  SweepParams sp;
+  int N;
+  double S;            // N * dxy
+  const double* rho2;  // device: squared uv extent of the observation
+  int Kc, nrw;         // kept window (same rule as the kernels' bounds)
+  void* F1;            // workspace: N x Kc complex
+  void* Gw;            // workspace: the window, nrw x Kc complex (+16 B)
+  GatherParams gp;
+  const void *u, *v, *re, *im, *w;
+  int64_t M;
+  double* partials;    // workspace: one slot per gather block
+  unsigned* counter;   // workspace: zero at rest
+  double* chi2_out;    // device result slot
+  size_t wbytes;       // window bytes staged in shared memory (0: read from L2)
+  bool edge;           // window reaches the edge of the half spectrum
+  int grid;            // gather blocks (those of a single call of this request)
+};
+
+// Launch shape of the batched passes.  Results do not depend on it (every
+// request keeps the block partition and reduction tree of a single call), so
+// it is free for the autotuner to choose.
+struct BatchShape {
+  int row_blocks;       // persistent row-pass blocks per SM and request group (1, 2, 4)
+  int jobs_per_launch;  // requests per launch (<= kBatchJobs)
+};
+
+// Batched passes: each launch covers up to jobs_per_launch requests of one
+// transform length (grid row y = request).  `tw[lg]` is the twiddle table of
+// length 2^lg.  `launches` is incremented per kernel launched.
+template <typename T> struct BatchLaunch {
+  static bool supported(int N);  // lengths the batched passes cover
+  static cudaError_t rows(const BatchItem* items, int n, const void* const* tw, int* err,
+                          const BatchShape& shape, int* launches, cudaStream_t st);
+  static cudaError_t cols(const BatchItem* items, int n, const void* const* tw,
+                          const BatchShape& shape, int* launches, cudaStream_t st);
+  static cudaError_t gather(const BatchItem* items, int n, const BatchShape& shape,
+                            int* launches, cudaStream_t st);
+};
+
 // Compile-time-length FFT passes (gal_fft3.cuh), instantiated per precision in
 // gal_fft3_f32.cu / gal_fft3_f64.cu.  They return cudaErrorNotSupported when
 // the length is outside their range (the caller then uses the generic passes).

@@ -107,6 +107,18 @@ template <typename T> struct SweepT {
   int nr;
 };
 
+// Per-request kernel arguments.  Every pass takes a fixed-size array of K jobs
+// as one __grid_constant__ parameter (read in place from the parameter bank,
+// never copied): a single call launches K = 1, a batch launches up to
+// kBatchJobs requests at once with job blockIdx.y in grid row y.
+template <typename J, int K> struct Jobs {
+  J j[K];
+};
+
+template <typename T> struct RowJob;
+template <typename T> struct ColJob;
+template <typename T> struct GatherJob;
+
 template <typename T> __host__ __device__ inline SweepT<T> sweep_cast(const SweepParams& p) {
   SweepT<T> q;
   q.Rmin = (T)p.Rmin;
@@ -297,12 +309,18 @@ template <typename T, int L, int NSEQ> struct Shape3 {
 // copies still in flight (bounded) and ends the block.
 // Otherwise (SWEEP, or an image that is not 16-byte aligned) each block loads
 // or generates its rows directly.
-template <typename T, int LG, bool TMA, bool SWEEP>
+template <typename T, int LG, bool TMA, bool SWEEP, int K>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads)
-row_fft3_kernel(const T* __restrict__ image, const T* __restrict__ I, SweepT<T> sp,
-                const cplx_t<T>* __restrict__ tw, cplx_t<T>* __restrict__ F1,
-                const double* __restrict__ rho2, double S, int* __restrict__ err) {
+row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
+                int* __restrict__ err) {
   using C = cplx_t<T>;
+  const RowJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
+  const T* __restrict__ image = jb.image;
+  const T* __restrict__ I = jb.I;
+  const SweepT<T>& sp = jb.sp;
+  C* __restrict__ F1 = jb.F1;
+  const double* __restrict__ rho2 = jb.rho2;
+  const double S = jb.S;
   constexpr int M = 1 << LG, N = 2 * M;
   using SH = Shape3<T, M, N>;
   using P = typename SH::P;
@@ -446,11 +464,15 @@ __device__ __forceinline__ void l2_prefetch(const L2Prefetch& pf, int tid, int n
   }
 }
 
-template <typename T, int LG>
+template <typename T, int LG, int K>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads)
-col_fft3_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gw,
-                const cplx_t<T>* __restrict__ tw, const double* __restrict__ rho2, double S,
+col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
                 int col_blocks, L2Prefetch pf) {
+  const ColJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
+  const cplx_t<T>* __restrict__ F1 = jb.F1;
+  cplx_t<T>* __restrict__ Gw = jb.Gw;
+  const double* __restrict__ rho2 = jb.rho2;
+  const double S = jb.S;
   if ((int)blockIdx.x >= col_blocks) {
     l2_prefetch(pf, (blockIdx.x - col_blocks) * blockDim.x + threadIdx.x,
                 (gridDim.x - col_blocks) * blockDim.x);
@@ -575,6 +597,21 @@ template <> struct GatherT<float> {
   }
 };
 
+template <typename T> struct RowJob {
+  const T* image;       // nxy x nxy image (null when swept from I)
+  const T* I;           // profile (SWEEP)
+  SweepT<T> sp;
+  cplx_t<T>* F1;        // row-pass output, pitch Kc
+  const double* rho2;   // squared uv extent of the request's points
+  double S;             // nxy * dxy
+};
+template <typename T> struct ColJob {
+  const cplx_t<T>* F1;
+  cplx_t<T>* Gw;        // window output, nrw x Kc
+  const double* rho2;
+  double S;
+};
+
 template <> struct GatherT<double> {
   double cpa, spa, S, phx, phy;
   double Sd;
@@ -590,6 +627,19 @@ template <> struct GatherT<double> {
     r.N = g.N;
     return r;
   }
+};
+
+template <typename T> struct GatherJob {
+  const cplx_t<T>* Gw;
+  GatherT<T> p;
+  const double* rho2;
+  const T *u, *v, *re, *im, *w;
+  int64_t M;
+  int vec;              // all point arrays 16-byte aligned
+  cplx_t<T>* vis;       // sample mode output
+  double* partials;     // chi2 mode: one slot per block of the request
+  unsigned* counter;    // chi2 mode: last-block-done counter (self-resetting)
+  double* chi2_out;
 };
 
 // a * b exactly as hi + lo (b float-float): hi = a b.hi rounded, lo = the rest
@@ -1019,14 +1069,25 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 // shared memory (32 warps share one copy), 256-thread blocks otherwise
 template <bool SMEM> constexpr int gather_threads() { return SMEM ? 1024 : 256; }
 
-template <typename T, bool CHI2, bool SMEM, bool EDGE>
+template <typename T, bool CHI2, bool SMEM, bool EDGE, int K>
 __global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 1 : 3)
-gather_kernel(const cplx_t<T>* __restrict__ Gw, GatherT<T> p, const double* __restrict__ rho2,
-              const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ re,
-              const T* __restrict__ im, const T* __restrict__ w, int64_t M, int vec,
-              cplx_t<T>* __restrict__ vis, double* __restrict__ partials,
-              unsigned* __restrict__ counter, double* __restrict__ chi2_out, int smem_nodes) {
+gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes) {
   using C = cplx_t<T>;
+  const GatherJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
+  const C* __restrict__ Gw = jb.Gw;
+  const GatherT<T>& p = jb.p;
+  const double* __restrict__ rho2 = jb.rho2;
+  const T* __restrict__ u = jb.u;
+  const T* __restrict__ v = jb.v;
+  const T* __restrict__ re = jb.re;
+  const T* __restrict__ im = jb.im;
+  const T* __restrict__ w = jb.w;
+  const int64_t M = jb.M;
+  const int vec = jb.vec;
+  C* __restrict__ vis = jb.vis;
+  double* __restrict__ partials = jb.partials;
+  unsigned* __restrict__ counter = jb.counter;
+  double* __restrict__ chi2_out = jb.chi2_out;
   const Bounds bd = block_bounds(rho2, p.Sd, p.N);
   const Window win = make_window(bd, p.N);
   typename Acc<T>::type acc;
@@ -1127,16 +1188,16 @@ template <typename T> cudaError_t Launch<T>::init() {
     return e;
   // the gather also holds a little static shared memory (reduction scratch),
   // so its dynamic budget stays below the per-block total
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, true>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, true, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, false>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, true, true, false, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, true>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, true, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
-  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, false>,
+  if ((e = cudaFuncSetAttribute(gather_kernel<T, false, true, false, 1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxWindowSmem)))
     return e;
   return cudaFuncSetAttribute(col_pass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1147,16 +1208,16 @@ template <typename T> int Launch<T>::gather_blocks_per_sm(bool chi2, size_t wind
   int n = 0;
   if (window_smem) {
     if (chi2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true, true>,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, true, true, 1>,
                                                     gather_threads<true>(), window_smem);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true, true>,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, true, true, 1>,
                                                     gather_threads<true>(), window_smem);
   } else {
     if (chi2)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false, true>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, true, false, true, 1>, 256, 0);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, false, true>, 256, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gather_kernel<T, false, false, true, 1>, 256, 0);
   }
   return n < 1 ? 1 : n;
 }
@@ -1274,24 +1335,23 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
     if (need < 1) need = 1;
     if (need < grid) grid = (int)need;
   }
-  C* vo = static_cast<C*>(vis);
-  auto go = [&](auto kern, size_t smem) {
-    kern<<<grid, threads, smem, st>>>(g, p, rho2, u, v, re, im, w, M, vec, vo, partials, counter,
-                                      chi2, nodes);
-  };
+  Jobs<GatherJob<T>, 1> jb;
+  jb.j[0] = GatherJob<T>{g, p, rho2, u, v, re, im, w, M, vec, static_cast<C*>(vis), partials,
+                         counter, chi2};
+  auto go = [&](auto kern, size_t smem) { kern<<<grid, threads, smem, st>>>(jb, nodes); };
   if (chi2) {
     if (window_smem)
-      edge ? go(gather_kernel<T, true, true, true>, window_smem)
-           : go(gather_kernel<T, true, true, false>, window_smem);
+      edge ? go(gather_kernel<T, true, true, true, 1>, window_smem)
+           : go(gather_kernel<T, true, true, false, 1>, window_smem);
     else
-      edge ? go(gather_kernel<T, true, false, true>, 0) : go(gather_kernel<T, true, false, false>, 0);
+      edge ? go(gather_kernel<T, true, false, true, 1>, 0) : go(gather_kernel<T, true, false, false, 1>, 0);
   } else {
     if (window_smem)
-      edge ? go(gather_kernel<T, false, true, true>, window_smem)
-           : go(gather_kernel<T, false, true, false>, window_smem);
+      edge ? go(gather_kernel<T, false, true, true, 1>, window_smem)
+           : go(gather_kernel<T, false, true, false, 1>, window_smem);
     else
-      edge ? go(gather_kernel<T, false, false, true>, 0)
-           : go(gather_kernel<T, false, false, false>, 0);
+      edge ? go(gather_kernel<T, false, false, true, 1>, 0)
+           : go(gather_kernel<T, false, false, false, 1>, 0);
   }
   return cudaGetLastError();
 }

@@ -225,3 +225,88 @@ def large_image_problem(nxy: int = 4096, M: int = 5_000_000, seed: int = 2) -> I
     dRA, dDec = rng.uniform(-0.1, 0.1, 2) * ARCSEC
     PA = rng.uniform(0.0, math.pi)
     return ImageProblem(img, dxy, u, v, w, nre, nim, float(dRA), float(dDec), float(PA))
+
+
+def keplerian_channel(nxy: int, dxy: float, v_chan: float, r_c: float = 0.8 * ARCSEC,
+                      inc: float = 40.0 * DEG, pa: float = 30.0 * DEG, mstar: float = 1.0,
+                      dist_pc: float = 140.0, sigma_v: float = 0.25,
+                      flux_scale: float = 1.0) -> np.ndarray:
+    """One channel map of a Keplerian disc's line emission (Jy/pixel).
+
+    I(r, phi) ~ exp(-r/r_c) exp(-(v_chan - v_K(r) sin(inc) cos(phi))^2 / (2 sigma_v^2)),
+    v_K = 29.78 km/s sqrt(mstar / r[au]) with r[au] = r["] * dist_pc; (r, phi)
+    are disc-plane polar coordinates of the sky pixel (inclination inc, major
+    axis at position angle pa East of North); velocities in km/s.
+    """
+    c = (np.arange(nxy) - nxy // 2) * dxy
+    x = -c[None, :]                     # East to the left, as in the pixel convention
+    y = c[:, None]
+    cp, sp = math.cos(pa), math.sin(pa)
+    xm = x * sp + y * cp                # along the major axis
+    ym = (-x * cp + y * sp) / math.cos(inc)
+    r = np.sqrt(xm * xm + ym * ym)
+    cosphi = np.where(r > 0, xm / np.maximum(r, 1e-30), 0.0)
+    r_au = np.maximum(r / ARCSEC * dist_pc, 1e-3)
+    vk = 29.78 * np.sqrt(mstar / r_au)
+    line = np.exp(-((v_chan - vk * math.sin(inc) * cosphi) ** 2) / (2.0 * sigma_v ** 2))
+    img = np.exp(-r / r_c) * line
+    total = img.sum()
+    return (img * (flux_scale / total if total > 0 else 0.0))
+
+
+@dataclass
+class CubeChannel:
+    image: np.ndarray
+    dxy: float
+    u: np.ndarray
+    v: np.ndarray
+    w: np.ndarray
+    noise_re: np.ndarray
+    noise_im: np.ndarray
+    dRA: float
+    dDec: float
+    PA: float
+
+
+def spectral_cube(n_chan: int = 128, sizes=(512, 1024, 2048), m_lo: int = 100_000,
+                  m_hi: int = 2_000_000, fov: float = 5.12 * ARCSEC, seed: int = 3,
+                  base_uv=None) -> list[CubeChannel]:
+    """Channels of a Keplerian disc cube: per channel a side drawn uniformly
+    from ``sizes`` (pixel size fov / side), an observation of M_c ~ U[m_lo, m_hi]
+    points subsampled from the ALMA-like layout and scaled by the channel
+    frequency (line at 100 GHz, channels 0.5 km/s apart), w ~ U[0.5, 2] and
+    noise sigma = 1/sqrt(w).  One set of dRA, dDec, PA for the cube."""
+    rng = np.random.default_rng(seed)
+    if base_uv is None:
+        base_uv = alma_like_uv(m_hi, rng)
+    bu, bv = base_uv
+    dRA, dDec = (float(a) for a in rng.uniform(-0.1, 0.1, 2) * ARCSEC)
+    PA = float(rng.uniform(0.0, math.pi))
+    dv = 0.5
+    out = []
+    for k in range(n_chan):
+        nxy = int(sizes[rng.integers(len(sizes))])
+        dxy = fov / nxy
+        v_chan = (k - (n_chan - 1) / 2) * dv
+        scale = 1.0 - v_chan / 299792.458          # frequency of the channel / line frequency
+        m = int(rng.integers(m_lo, m_hi + 1))
+        sel = rng.choice(bu.size, size=m, replace=False) if m < bu.size else np.arange(bu.size)
+        w = weights_uniform(m, rng)
+        nre, nim = noise(w, rng)
+        out.append(CubeChannel(keplerian_channel(nxy, dxy, v_chan).astype(np.float64), dxy,
+                               bu[sel] * scale, bv[sel] * scale, w, nre, nim, dRA, dDec, PA))
+    return out
+
+
+def walker_params(n: int = 64, seed: int = 4) -> list[dict]:
+    """Random ring-profile and geometry parameters for MCMC walkers: ring
+    radius U[0.3", 0.7"], width U[0.05", 0.15"], power-law exponent U[-1, 0],
+    inclination U[0, 70 deg], PA U[0, pi), dRA/dDec U[-0.1", 0.1"]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        out.append(dict(r0=rng.uniform(0.3, 0.7) * ARCSEC, width=rng.uniform(0.05, 0.15) * ARCSEC,
+                        power=rng.uniform(-1.0, 0.0), inc=rng.uniform(0.0, 70.0) * DEG,
+                        PA=rng.uniform(0.0, math.pi), dRA=rng.uniform(-0.1, 0.1) * ARCSEC,
+                        dDec=rng.uniform(-0.1, 0.1) * ARCSEC))
+    return out

@@ -1,0 +1,175 @@
+"""Batched chi-square (gal_chi2_batch) and its CUDA-graph form.
+
+Every batched result must be bitwise equal to the single call of the same
+request on the same context (same kernels, block partitions and reduction
+trees); a few are also checked against the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_06999_gb300 import Context, GalError, Request, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_CHI2 = {torch.float64: 1e-12, torch.float32: 1e-6}
+
+
+def dev(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+
+
+def make_obs(ctx, u, v, w, nre, nim, dt):
+    # observed = noise only: the chi-square then sums model power plus noise
+    return ctx.register(dev(u, dt), dev(v, dt), dev(nre, dt), dev(nim, dt), dev(w, dt))
+
+
+def single(ctx, r: Request):
+    if r.image is not None:
+        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA)
+    return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
+                            r.PA)
+
+
+def mixed_requests(ctx, dt, seed=0, n_img=10, n_prof=6):
+    """Cube channels of several sides plus profile walkers sharing one dataset."""
+    rng = np.random.default_rng(seed)
+    cube = synth.spectral_cube(n_chan=n_img, sizes=(32, 64, 128, 256), m_lo=2_000, m_hi=30_000,
+                               seed=seed)
+    reqs, keep = [], []
+    for ch in cube:
+        obs = make_obs(ctx, ch.u, ch.v, ch.w, ch.noise_re, ch.noise_im, dt)
+        img = dev(ch.image, dt)
+        keep.append((obs, img))
+        reqs.append(Request(obs, image=img, dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec, PA=ch.PA))
+    q = synth.profile_problem(nxy=128, M=20_000, nr=512, seed=seed + 1, dxy=0.04 * synth.ARCSEC)
+    obs = make_obs(ctx, q.u, q.v, q.w, q.noise_re, q.noise_im, dt)
+    keep.append(obs)
+    for p in synth.walker_params(n_prof, seed=seed + 2):
+        I = dev(synth.ring_profile(512, q.dR, q.Rmin, p["r0"], p["width"], p["power"]), dt)
+        keep.append(I)
+        reqs.append(Request(obs, intensity=I, nxy=q.nxy, dxy=q.dxy, Rmin=q.Rmin, dR=q.dR,
+                            inc=p["inc"], dRA=p["dRA"], dDec=p["dDec"], PA=p["PA"]))
+    order = rng.permutation(len(reqs))
+    return [reqs[i] for i in order], keep
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_batch_equals_single_calls_bitwise(dt):
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, dt)
+    got = ctx.chi2_batch(reqs)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    assert torch.equal(got, want), (got - want).abs().max().item()
+    assert all(math.isfinite(x) and x > 0 for x in got.tolist())
+
+
+def test_batch_matches_oracle():
+    ctx = Context(0)
+    dt = torch.float32
+    reqs, keep = mixed_requests(ctx, dt, seed=5, n_img=3, n_prof=2)
+    got = ctx.chi2_batch(reqs).cpu().numpy()
+    for r, g in zip(reqs, got):
+        o = r.obs
+        u, v, re, im, w = (t.double().cpu().numpy() for t in o._tensors)
+        if r.image is not None:
+            ref = oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w,
+                                    r.dRA, r.dDec, r.PA)
+        else:
+            ref = oracle.chi2_profile(r.intensity.double().cpu().numpy(), r.Rmin, r.dR, r.nxy,
+                                      r.dxy, u, v, re, im, w, r.dRA, r.dDec, r.PA, r.inc)
+        assert abs(g - ref) <= TOL_CHI2[dt] * abs(ref), (g, ref)
+
+
+def test_more_than_one_launch_per_pass_and_odd_members():
+    """40 requests of one side (two chunks), an unbatchable side, an empty
+    observation and a mix of precisions in one call."""
+    ctx = Context(0)
+    rng = np.random.default_rng(9)
+    reqs, keep = [], []
+    p = synth.small_image_problem(nxy=64, M=3_000, seed=9)
+    obs32 = make_obs(ctx, p.u, p.v, p.w, p.noise_re, p.noise_im, torch.float32)
+    obs64 = make_obs(ctx, p.u, p.v, p.w, p.noise_re, p.noise_im, torch.float64)
+    empty = ctx.register(*(torch.empty(0, dtype=torch.float32, device="cuda") for _ in range(5)))
+    for k in range(40):
+        img = dev(p.image * (1.0 + 0.01 * k), torch.float32)
+        keep.append(img)
+        reqs.append(Request(obs32, image=img, dxy=p.dxy, dRA=p.dRA, PA=0.1 * k))
+    small = dev(p.image[24:40, 24:40], torch.float32)          # nxy = 16: single-call path
+    reqs.append(Request(obs32, image=small, dxy=p.dxy))
+    reqs.append(Request(empty, image=dev(p.image, torch.float32), dxy=p.dxy))
+    img64 = dev(p.image, torch.float64)
+    reqs.append(Request(obs64, image=img64, dxy=p.dxy, dDec=p.dDec))
+    keep += [small, img64]
+    order = rng.permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
+    got = ctx.chi2_batch(reqs)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    assert torch.equal(got, want)
+    k_empty = [i for i, r in enumerate(reqs) if r.obs is empty][0]
+    assert got[k_empty].item() == 0.0
+
+
+def test_tuning_does_not_change_results():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=3, n_img=6, n_prof=3)
+    ctx.set_batch_tuning(False)
+    a = ctx.chi2_batch(reqs)
+    ctx2 = Context(0)
+    ctx2.set_batch_tuning(True)
+    reqs2 = [Request(ctx2.register(*r.obs._tensors), image=r.image, intensity=r.intensity,
+                     nxy=r.nxy, dxy=r.dxy, dRA=r.dRA, dDec=r.dDec, PA=r.PA, Rmin=r.Rmin, dR=r.dR,
+                     inc=r.inc) for r in reqs]
+    b = ctx2.chi2_batch(reqs2)
+    c = ctx2.chi2_batch(reqs2)   # cached shape
+    assert torch.equal(a, b) and torch.equal(b, c)
+
+
+def test_graph_replay_update_and_regrowth():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=7, n_img=5, n_prof=3)
+    g = ctx.capture_batch(reqs)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    out = g.launch().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(out, want)
+    # rewrite one image and one profile in place: the replay sees the new values
+    ki = next(i for i, r in enumerate(reqs) if r.image is not None)
+    kp = next(i for i, r in enumerate(reqs) if r.intensity is not None)
+    reqs[ki].image.mul_(0.5)
+    reqs[kp].intensity.mul_(2.0)
+    out = g.launch().clone()
+    want = torch.stack([single(ctx, r) for r in reqs])
+    assert torch.equal(out, want)
+    # new scalars, same structure: update in place
+    new = [Request(r.obs, image=r.image, intensity=r.intensity, nxy=r.nxy, dxy=r.dxy,
+                   dRA=r.dRA + 1e-7, dDec=r.dDec, PA=r.PA + 0.3, Rmin=r.Rmin, dR=r.dR, inc=r.inc)
+           for r in reqs]
+    g.update(new)
+    out = g.launch().clone()
+    want = torch.stack([single(ctx, r) for r in new])
+    assert torch.equal(out, want)
+    # a bigger batch reallocates the workspace; the graph re-records itself
+    big, keep2 = mixed_requests(ctx, torch.float32, seed=8, n_img=12, n_prof=4)
+    ctx.chi2_batch(big)
+    out = g.launch().clone()
+    assert torch.equal(out, want)
+    # a different structure is refused
+    with pytest.raises(GalError):
+        g.update(new[:-1])
+    g.close()
+
+
+def test_invalid_request_launches_nothing():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=11, n_img=2, n_prof=1)
+    n0 = ctx.launch_count()
+    bad = list(reqs) + [Request(reqs[0].obs, image=reqs[0].image, dxy=-1.0)]
+    with pytest.raises(GalError):
+        ctx.chi2_batch(bad)
+    assert ctx.launch_count() == n0
+    out = ctx.chi2_batch([])
+    assert out.numel() == 0
