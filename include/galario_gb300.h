@@ -52,6 +52,8 @@ extern "C" {
 #define GAL_E_CUDA     -3   /* a CUDA runtime call failed */
 #define GAL_E_RANGE    -4   /* internal index check tripped (see gal_check) */
 #define GAL_E_DEVICE   -5   /* no usable CUDA device / wrong architecture */
+#define GAL_E_BUSY     -6   /* server: queue full (submit) */
+#define GAL_E_TIMEOUT  -7   /* server: the result was not ready within the wait's limit */
 
 typedef struct gal_ctx gal_ctx;     /* workspace, twiddle tables, launch shapes, counters */
 typedef struct gal_data gal_data;   /* a registered observation: u, v, Re, Im, w + uv extent */
@@ -88,19 +90,27 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4);
 
 /* ---- observations ------------------------------------------------------------------- */
 
+/* Device workspace the context holds now (spectra, windows, partial sums,
+ * twiddles, staging), in bytes; and the device it was created on. */
+size_t gal_workspace_bytes(const gal_ctx* ctx);
+int gal_device(const gal_ctx* ctx);
+
 /* Register an observation of M visibilities: u, v (wavelengths), Re_obs, Im_obs (Jy)
  * and weights w = 1/sigma^2 (Sect. 3.1, Eq. chap6.eq:def.chi.square).  The arrays
  * are borrowed (device memory, must outlive the handle).  Enqueues on `stream` one
  * reduction for the largest baseline sqrt(u^2+v^2) (Sect. 3.3, criterion (i)),
  * which later calls use to restrict the FFT to the part of the spectrum the uv
  * points can reach (an exact pruning), and reads that one value back
- * (synchronising `stream` once). */
+ * (synchronising `stream` once).  The handle may be used by every context on
+ * the same device. */
 int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
                         const float* im, const float* w, int64_t M, void* stream, gal_data** out);
 int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
                         const double* im, const double* w, int64_t M, void* stream, gal_data** out);
 /* Release a handle (not the borrowed arrays).  Waits for the device. */
 void gal_data_destroy(gal_data* data);
+/* Number of visibilities and bytes per real value (4 or 8) of a handle. */
+int gal_data_info(const gal_data* data, int64_t* M_out, int* real_bytes_out);
 
 /* ---- the operations of Fig. 3 --------------------------------------------------------- */
 
@@ -223,6 +233,60 @@ int gal_chi2_batch_capture(gal_ctx* ctx, const gal_request* reqs, int n, double*
 int gal_graph_update(gal_graph* g, const gal_request* reqs, int n, double* chi2_out);
 int gal_graph_launch(gal_graph* g, void* stream);
 void gal_graph_destroy(gal_graph* g);
+
+/* ---- serving ------------------------------------------------------------------------- */
+
+/* A request loop for chi-square requests of mixed kinds and sizes on one GPU
+ * (the paper has no counterpart; it serves many independent evaluations the
+ * way an MCMC or a fitting service issues them).
+ *
+ * A scheduler thread owns `slots` worker contexts, each with its own CUDA
+ * stream.  Submitted requests wait in a FIFO queue.  Whenever a slot is free
+ * the scheduler admits the head of the queue -- together with up to
+ * max_batch - 1 more queued requests of the same precision, run as one
+ * gal_chi2_batch -- if the HBM budget allows, so requests that arrive while
+ * others are on the GPU join as slots and memory free up and their work
+ * overlaps on the device.  Budget: the bytes of the observations added with
+ * gal_server_add_data plus the workspace every slot holds, where a slot about
+ * to take a launch is charged the workspace that launch may grow it to
+ * (3 half spectra of each request's side and precision).  The head request
+ * waits while that sum would exceed hbm_budget_bytes; one that can never fit
+ * fails with GAL_E_NOMEM.  Each result is bitwise equal to a single call of
+ * the request (batching does not change it).
+ *
+ * Observations must be added with gal_server_add_data_* (the budget counts
+ * them); a request's arrays (image or profile) must stay valid until its
+ * result has been waited for.  Latency is measured on the host from submit to
+ * the scheduler's observation that the result is in host memory. */
+typedef struct gal_server gal_server;
+int gal_server_create(int device, size_t hbm_budget_bytes, int slots, int max_batch,
+                      gal_server** out);
+/* As gal_data_create_*, on the server's device, charged to its budget
+ * (5 M real values; GAL_E_NOMEM if over).  Destroyed with the server. */
+int gal_server_add_data_f32(gal_server* s, const float* u, const float* v, const float* re,
+                            const float* im, const float* w, int64_t M, gal_data** out);
+int gal_server_add_data_f64(gal_server* s, const double* u, const double* v, const double* re,
+                            const double* im, const double* w, int64_t M, gal_data** out);
+/* Queue one request (copied); *ticket identifies it.  GAL_E_INVAL for an invalid
+ * request, GAL_E_BUSY when 65536 requests are already waiting. */
+int gal_server_submit(gal_server* s, const gal_request* req, uint64_t* ticket);
+/* Queue n requests at once (tickets[n]): all or none (GAL_E_INVAL / GAL_E_BUSY). */
+int gal_server_submit_many(gal_server* s, const gal_request* reqs, int n, uint64_t* tickets);
+/* Wait up to timeout_ms (< 0: forever) for a ticket: its chi-square and its
+ * latency in seconds.  Returns the request's own status (GAL_OK, or the error
+ * its evaluation met), GAL_E_TIMEOUT if not finished in time, GAL_E_INVAL for
+ * an unknown or already collected ticket.  A collected ticket is forgotten. */
+int gal_server_wait(gal_server* s, uint64_t ticket, int timeout_ms, double* chi2,
+                    double* latency_s);
+typedef struct gal_server_stats {
+  uint64_t submitted, completed, launches;  /* launches: single calls + batches */
+  uint64_t max_inflight;                    /* most requests on the GPU at once */
+  size_t data_bytes, workspace_bytes;       /* charged to the budget now */
+  size_t peak_bytes;                        /* largest charge seen */
+} gal_server_stats;
+int gal_server_get_stats(gal_server* s, gal_server_stats* out);
+/* Finish every queued request, stop the scheduler, free everything. */
+void gal_server_destroy(gal_server* s);
 
 /* ---- image sizing --------------------------------------------------------------------- */
 

@@ -7,6 +7,6 @@ CUDA kernels behind a C ABI (include/galario_gb300.h).
     obs = ctx.register(u, v, re, im, w)            # device tensors, float32 or float64
     chi2 = ctx.chi2_image(image, dxy, obs, dRA, dDec, PA)
 """
-from .api import (BatchGraph, Context, GalError, Observation, Request,  # noqa: F401
+from .api import (BatchGraph, Context, GalError, Observation, Request, Server,  # noqa: F401
                   chi2_image, chi2_profile, default_context, get_image_size, sample_image,
                   sample_profile, sweep)

@@ -50,7 +50,26 @@ class GalRequest(ct.Structure):
                 ("data", P)]
 
 
+class GalServerStats(ct.Structure):
+    """struct gal_server_stats of include/galario_gb300.h."""
+    _fields_ = [("submitted", ct.c_uint64), ("completed", ct.c_uint64),
+                ("launches", ct.c_uint64), ("max_inflight", ct.c_uint64),
+                ("data_bytes", ct.c_size_t), ("workspace_bytes", ct.c_size_t),
+                ("peak_bytes", ct.c_size_t)]
+
+
 _SIGNATURES.update({
+    "gal_workspace_bytes": (ct.c_size_t, [P]),
+    "gal_device": (I32, [P]),
+    "gal_data_info": (I32, [P, ct.POINTER(I64), ct.POINTER(I32)]),
+    "gal_server_create": (I32, [I32, ct.c_size_t, I32, I32, ct.POINTER(P)]),
+    "gal_server_add_data_f32": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
+    "gal_server_add_data_f64": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
+    "gal_server_submit": (I32, [P, ct.POINTER(GalRequest), ct.POINTER(ct.c_uint64)]),
+    "gal_server_submit_many": (I32, [P, ct.POINTER(GalRequest), I32, ct.POINTER(ct.c_uint64)]),
+    "gal_server_wait": (I32, [P, ct.c_uint64, I32, ct.POINTER(D), ct.POINTER(D)]),
+    "gal_server_get_stats": (I32, [P, ct.POINTER(GalServerStats)]),
+    "gal_server_destroy": (None, [P]),
     "gal_chi2_batch": (I32, [P, ct.POINTER(GalRequest), I32, P, P]),
     "gal_set_batch_tuning": (I32, [P, I32]),
     "gal_chi2_batch_capture": (I32, [P, ct.POINTER(GalRequest), I32, P, P, ct.POINTER(P)]),

@@ -333,6 +333,103 @@ class Context:
         return n.value, d.value
 
 
+class ServedData:
+    """An observation held by a Server (borrowed tensors kept alive here)."""
+
+    def __init__(self, handle, tensors):
+        self.handle = handle
+        self._tensors = tensors
+        self.dtype = tensors[0].dtype
+
+
+class Server:
+    """The request loop of gal_server_*: a FIFO of chi-square requests served
+    by `slots` worker contexts under an HBM budget, with queued requests of
+    one precision admitted together as one batch (up to max_batch)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 150 * 10**9, slots: int = 4,
+                 max_batch: int = 16):
+        self.lib = _native.load()
+        self.device = torch.device("cuda", device)
+        h = ct.c_void_p()
+        _check(None, self.lib.gal_server_create(device, int(hbm_budget), slots, max_batch,
+                                                ct.byref(h)))
+        self.handle = h.value
+        self._data = []
+        self._inflight = {}
+
+    def add_data(self, u, v, re, im, w) -> ServedData:
+        tensors = [t.to(self.device).contiguous() for t in (u, v, re, im, w)]
+        m = tensors[0].numel()
+        if any(t.numel() != m for t in tensors):
+            raise ValueError("u, v, re, im, w must have the same length")
+        sfx = _suffix(*tensors)
+        h = ct.c_void_p()
+        fn = getattr(self.lib, f"gal_server_add_data_{sfx}")
+        _check(None, fn(self.handle, *[t.data_ptr() for t in tensors], m, ct.byref(h)))
+        d = ServedData(ct.c_void_p(h.value), tensors)
+        self._data.append(d)
+        return d
+
+    def _struct(self, req: "Request"):
+        if req.image is not None:
+            t = req.image.to(self.device).contiguous()
+            st = _native.GalRequest(t.data_ptr(), None, 0, 0.0, 0.0, 0.0, req.nxy, req.dxy,
+                                    req.dRA, req.dDec, req.PA, req.obs.handle.value)
+        else:
+            t = req.intensity.to(self.device).contiguous()
+            st = _native.GalRequest(None, t.data_ptr(), t.numel(), req.Rmin, req.dR, req.inc,
+                                    req.nxy, req.dxy, req.dRA, req.dDec, req.PA,
+                                    req.obs.handle.value)
+        if t.dtype != req.obs.dtype:
+            raise TypeError("model dtype must match the observation's")
+        return st, t
+
+    def submit(self, req: "Request") -> int:
+        """Queue a Request whose `obs` is a ServedData; returns its ticket."""
+        st, t = self._struct(req)
+        tk = ct.c_uint64()
+        _check(None, self.lib.gal_server_submit(self.handle, ct.byref(st), ct.byref(tk)))
+        self._inflight[tk.value] = t           # keep the model alive until collected
+        return tk.value
+
+    def submit_many(self, reqs) -> list:
+        """Queue several Requests at once (they reach the queue together)."""
+        pairs = [self._struct(r) for r in reqs]
+        arr = (_native.GalRequest * max(1, len(pairs)))(*[p[0] for p in pairs])
+        tks = (ct.c_uint64 * max(1, len(pairs)))()
+        _check(None, self.lib.gal_server_submit_many(self.handle, arr, len(pairs), tks))
+        for k, (_, t) in enumerate(pairs):
+            self._inflight[tks[k]] = t
+        return [tks[k] for k in range(len(pairs))]
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(chi2, latency in seconds) of a ticket."""
+        c, lat = ct.c_double(), ct.c_double()
+        st = self.lib.gal_server_wait(self.handle, ticket, timeout_ms, ct.byref(c), ct.byref(lat))
+        if st != -7:
+            self._inflight.pop(ticket, None)
+        _check(None, st)
+        return c.value, lat.value
+
+    def stats(self) -> dict:
+        s = _native.GalServerStats()
+        _check(None, self.lib.gal_server_get_stats(self.handle, ct.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.gal_server_destroy(self.handle)
+            self.handle = None
+            self._inflight.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 _default: dict[int, Context] = {}
 
 

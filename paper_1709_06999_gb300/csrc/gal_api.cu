@@ -75,7 +75,8 @@ struct gal_ctx {
 };
 
 struct gal_data {
-  gal_ctx* ctx = nullptr;
+  gal_ctx* ctx = nullptr;  // the context it was registered on
+  int device = 0;          // usable by every context on this device
   int real_bytes = 0;
   int64_t M = 0;
   const void *u = nullptr, *v = nullptr, *re = nullptr, *im = nullptr, *w = nullptr;
@@ -306,7 +307,7 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
               double dxy, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
               cudaStream_t st) {
   if (!ctx || !d || !chi2) return GAL_E_INVAL;
-  if (d->ctx != ctx || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
+  if (d->device != ctx->device || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
   if (!aligned(chi2, sizeof(double))) return GAL_E_INVAL;
   if (d->M == 0) {
@@ -395,6 +396,7 @@ int data_create_t(gal_ctx* ctx, const T* u, const T* v, const T* re, const T* im
   gal_data* d = new (std::nothrow) gal_data;
   if (!d) return GAL_E_NOMEM;
   d->ctx = ctx;
+  d->device = ctx->device;
   d->real_bytes = sizeof(T);
   d->M = M;
   d->u = u;
@@ -497,7 +499,7 @@ struct BatchPlan {
 
 int check_request(gal_ctx* ctx, const gal_request& r) {
   const gal_data* d = r.data;
-  if (!d || d->ctx != ctx) return GAL_E_INVAL;
+  if (!d || d->device != ctx->device) return GAL_E_INVAL;
   GAL_TRY(check_geometry(r.nxy, r.dxy));
   if (!std::isfinite(r.dRA) || !std::isfinite(r.dDec) || !std::isfinite(r.PA)) return GAL_E_INVAL;
   const size_t rb = (size_t)d->real_bytes;
@@ -812,6 +814,8 @@ const char* gal_strerror(int s) {
     case GAL_E_CUDA: return "CUDA error";
     case GAL_E_RANGE: return "internal index check tripped";
     case GAL_E_DEVICE: return "no usable CUDA device";
+    case GAL_E_BUSY: return "queue full or request not finished";
+    case GAL_E_TIMEOUT: return "wait timed out";
     default: return "unknown status";
   }
 }
@@ -919,6 +923,18 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4) {
   return GAL_OK;
 }
 
+size_t gal_workspace_bytes(const gal_ctx* ctx) {
+  if (!ctx) return 0;
+  size_t b = ctx->F1_bytes + ctx->Gw_bytes + ctx->batch_ws_bytes + ctx->stage_img_bytes +
+             ctx->batch_ctr_n * sizeof(unsigned) + sizeof(double) * (size_t)ctx->partials_len;
+  for (int p = 0; p < 2; ++p)
+    for (int l = 0; l <= kMaxLog2; ++l)
+      if (ctx->tw[p][l]) b += ((size_t)1 << l) * (p ? 16 : 8);
+  return b;
+}
+
+int gal_device(const gal_ctx* ctx) { return ctx ? ctx->device : -1; }
+
 int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, void* stream) {
   if (!ctx || n < 0 || (n > 0 && (!reqs || !chi2_out))) return GAL_E_INVAL;
   if (n == 0) return GAL_OK;
@@ -1012,6 +1028,13 @@ int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const do
                         gal_data** out) {
   return data_create_t<double>(ctx, u, v, re, im, w, M, stream, out);
 }
+int gal_data_info(const gal_data* d, int64_t* M_out, int* real_bytes_out) {
+  if (!d) return GAL_E_INVAL;
+  if (M_out) *M_out = d->M;
+  if (real_bytes_out) *real_bytes_out = d->real_bytes;
+  return GAL_OK;
+}
+
 void gal_data_destroy(gal_data* d) {
   if (!d) return;
   cudaDeviceSynchronize();
