@@ -223,6 +223,197 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched and served throughput (extra measurements at N = 1)
+# ---------------------------------------------------------------------------
+def _timed(torch, fn, reps, flush=None):
+    """Mean device milliseconds of fn() over reps runs (events on the current stream)."""
+    total = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        total += a.elapsed_time(b)
+    return total / reps
+
+
+def _single(ctx, r, out=None):
+    if r.image is not None:
+        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, out=out)
+    return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
+                            r.PA, out=out)
+
+
+def measure_batched(torch, ctx, dev, flush, reps=3):
+    """Spectral cube (128 Keplerian channels, nxy in {512, 1024, 2048}, M_c in
+    [1e5, 2e6]) and 64 ring-profile walkers (nxy 1024, M 1e6 shared): one
+    gal_chi2_batch per set, its CUDA-graph replay, sequential FP32 single
+    calls and sequential FP64 single calls of the same requests."""
+    from paper_1709_06999_gb300 import Request, synth
+    d32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    sets = {}
+    cube = synth.spectral_cube(n_chan=128, seed=3)
+    r32, r64 = [], []
+    for ch in cube:
+        t32 = [d32(a) for a in (ch.u, ch.v, ch.noise_re, ch.noise_im, ch.w)]
+        o32 = ctx.register(*t32)
+        o64 = ctx.register(*[t.double() for t in t32])
+        img = d32(ch.image)
+        r32.append(Request(o32, image=img, dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec, PA=ch.PA))
+        r64.append(Request(o64, image=img.double(), dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec,
+                           PA=ch.PA))
+    sets["cube"] = (r32, r64, "128 Keplerian-disc channels, nxy U{512,1024,2048}, "
+                              "M_c U[1e5,2e6] (ALMA-like layout x channel frequency)")
+    q = synth.profile_problem(nxy=1024, M=1_000_000, nr=8192, seed=1)
+    t32 = [d32(a) for a in (q.u, q.v, q.noise_re, q.noise_im, q.w)]
+    o32 = ctx.register(*t32)
+    o64 = ctx.register(*[t.double() for t in t32])
+    w32, w64 = [], []
+    for wp in synth.walker_params(64):
+        I = d32(synth.ring_profile(8192, q.dR, q.Rmin, wp["r0"], wp["width"], wp["power"]))
+        kw = dict(nxy=q.nxy, dxy=q.dxy, Rmin=q.Rmin, dR=q.dR, inc=wp["inc"], dRA=wp["dRA"],
+                  dDec=wp["dDec"], PA=wp["PA"])
+        w32.append(Request(o32, intensity=I, **kw))
+        w64.append(Request(o64, intensity=I.double(), **kw))
+    sets["walkers"] = (w32, w64, "64 ring-profile walkers, nxy 1024, nr 8192, one M=1e6 "
+                                 "observation shared")
+    res = {}
+    for name, (a32, a64, desc) in sets.items():
+        n = len(a32)
+        out = ctx.chi2_batch(a32)                      # first call tunes the launch shape
+        seq = torch.stack([_single(ctx, r) for r in a32])
+        ref64 = torch.stack([_single(ctx, r) for r in a64])
+        torch.cuda.synchronize(dev)
+        l0 = ctx.launch_count()
+        ms_b = _timed(torch, lambda: ctx.chi2_batch(a32, out=out), reps, flush)
+        launches = (ctx.launch_count() - l0) // reps
+        g = ctx.capture_batch(a32)
+        g.launch()
+        ms_g = _timed(torch, g.launch, reps, flush)
+        outs = torch.empty(n, dtype=torch.float64, device=dev)
+        ms_s = _timed(torch, lambda: [_single(ctx, r, out=outs[k]) for k, r in enumerate(a32)],
+                      reps, flush)
+        ms_64 = _timed(torch, lambda: [_single(ctx, r, out=outs[k]) for k, r in enumerate(a64)],
+                       1, flush)
+        rel = ((out - ref64).abs() / ref64.abs()).max().item()
+        res[name] = {
+            "workload": desc, "requests": n,
+            "batched_evals_per_s": 1000.0 * n / ms_b, "graph_evals_per_s": 1000.0 * n / ms_g,
+            "single_fp32_evals_per_s": 1000.0 * n / ms_s,
+            "plain_fp64_evals_per_s": 1000.0 * n / ms_64,
+            "ms_per_batch": ms_b, "launches_per_batch": launches,
+            "bitwise_equal_to_single_calls": bool(torch.equal(out, seq)),
+            "max_rel_err_vs_fp64_path": rel,
+        }
+        g.close()
+    return res
+
+
+def measure_serving(torch, dev, seconds=2.0, rate=2000.0, seed=21):
+    """Poisson arrivals (rate/s) of chi2_image / chi2_profile requests (50/50),
+    nxy U{256..4096}, over 16 resident observations with M log-U[1e4, 5e6]:
+    the FP32 server (4 slots, batches of <= 16, 150 GB budget) against the
+    plain FP64 path (single calls, one at a time, in arrival order)."""
+    from paper_1709_06999_gb300 import Context, Request, Server, synth
+    rng = np.random.default_rng(seed)
+    d32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    sizes = (256, 512, 1024, 2048, 4096)
+    fov = 4096 * 0.002 * synth.ARCSEC
+    srv = Server(dev.index or 0, hbm_budget=150 * 10**9, slots=4, max_batch=16)
+    ctx64 = Context(dev.index or 0)
+    data32, data64 = [], []
+    for _ in range(16):
+        m = int(np.exp(rng.uniform(np.log(1e4), np.log(5e6))))
+        u, v = synth.alma_like_uv(m, rng)
+        w = synth.weights_uniform(m, rng)
+        nre, nim = synth.noise(w, rng)
+        t = [d32(a) for a in (u, v, nre, nim, w)]
+        data32.append(srv.add_data(*t))
+        data64.append(ctx64.register(*[x.double() for x in t]))
+    imgs = {s: d32(synth.large_image(s, fov / s, rng)) for s in sizes}
+    nr = 8192
+    dR = 4.5 * synth.ARCSEC * 1.6 / nr
+    prof = d32(synth.ring_profile(nr, dR, dR / 2))
+    n = int(rate * seconds)
+    trace = []
+    for _ in range(n):
+        k = int(rng.integers(16))
+        s = int(sizes[rng.integers(len(sizes))])
+        geo = dict(dxy=fov / s, dRA=float(rng.uniform(-0.1, 0.1) * synth.ARCSEC),
+                   dDec=float(rng.uniform(-0.1, 0.1) * synth.ARCSEC), PA=float(rng.uniform(0, np.pi)))
+        if rng.random() < 0.5:
+            trace.append((k, dict(image=True, nxy=s, **geo)))
+        else:
+            trace.append((k, dict(image=False, nxy=s, inc=float(rng.uniform(0, 1.2)), **geo)))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+
+    def make(k, spec, data, dt):
+        kw = {x: spec[x] for x in ("dxy", "dRA", "dDec", "PA")}
+        if spec["image"]:
+            img = imgs[spec["nxy"]]
+            return Request(data[k], image=img if dt == torch.float32 else img.double(), **kw)
+        I = prof if dt == torch.float32 else prof.double()
+        return Request(data[k], intensity=I, nxy=spec["nxy"], Rmin=dR / 2, dR=dR,
+                       inc=spec["inc"], **kw)
+
+    reqs32 = [make(k, sp, data32, torch.float32) for k, sp in trace]
+
+    def serve(reqs, times):
+        t0 = time.perf_counter()
+        tickets = []
+        for r, ta in zip(reqs, times):
+            while time.perf_counter() - t0 < ta:
+                pass
+            tickets.append(srv.submit(r))
+        return np.array([srv.wait(tk)[1] for tk in tickets])
+
+    # warm-up: the first 20% of the trace (every worker grows its workspaces)
+    n_warm = max(1, n // 5)
+    serve(reqs32[:n_warm], arrivals[:n_warm])
+    lat = serve(reqs32, arrivals)
+    span = max(float(np.max(arrivals + lat)), float(arrivals[-1]))
+    st = srv.stats()
+    srv.close()
+    # plain FP64: one single call at a time, in arrival order
+    imgs64 = {s: im.double() for s, im in imgs.items()}
+    prof64 = prof.double()
+    for s in sizes:
+        ctx64.chi2_image(imgs64[s], fov / s, data64[0])
+    torch.cuda.synchronize(dev)
+    out = torch.empty((), dtype=torch.float64, device=dev)
+    lat64 = np.empty(n)
+    t0 = time.perf_counter()
+    for i, ((k, sp), ta) in enumerate(zip(trace, arrivals)):
+        while time.perf_counter() - t0 < ta:
+            pass
+        if sp["image"]:
+            ctx64.chi2_image(imgs64[sp["nxy"]], sp["dxy"], data64[k], sp["dRA"], sp["dDec"],
+                             sp["PA"], out=out)
+        else:
+            ctx64.chi2_profile(prof64, dR / 2, dR, sp["nxy"], sp["dxy"], data64[k], sp["inc"],
+                               sp["dRA"], sp["dDec"], sp["PA"], out=out)
+        torch.cuda.synchronize(dev)
+        lat64[i] = time.perf_counter() - t0 - ta
+    span64 = float(np.max(arrivals + lat64))
+    ms = lambda x, q: float(np.percentile(x, q) * 1000.0)  # noqa: E731
+    return {
+        "workload": f"Poisson {rate:.0f} req/s for {seconds:.1f} s, chi2_image/chi2_profile 50/50, "
+                    "nxy U{256..4096}, 16 resident observations M log-U[1e4,5e6]",
+        "requests": n,
+        "fp32_server": {"p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99), "mean_ms": float(lat.mean() * 1e3),
+                        "throughput_req_per_s": n / span, "launches": st["launches"],
+                        "max_inflight": st["max_inflight"], "peak_hbm_bytes": st["peak_bytes"],
+                        "slots": 4, "max_batch": 16, "budget_bytes": 150 * 10**9},
+        "plain_fp64": {"p50_ms": ms(lat64, 50), "p99_ms": ms(lat64, 99),
+                       "mean_ms": float(lat64.mean() * 1e3), "throughput_req_per_s": n / span64},
+        "latency": "host clock, submit to result in host memory",
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -380,6 +571,9 @@ def run_gpu(args):
     }
     if base is not None:
         line["cpu_baseline"] = base
+    if world == 1 and not args.no_extras:
+        line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
+        line["serving"] = measure_serving(torch, dev)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -393,6 +587,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-evals", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (cube, walkers) and serving measurements")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # the timing rules need at least 3 warm-up steps
     if args.impl == "reference":
