@@ -39,7 +39,7 @@ struct TimedStage {
 struct gal_ctx {
   int device = 0;
   int num_sms = 0;
-  void* F1 = nullptr;  // row-pass output (nxy x Kc complex)
+  void* F1 = nullptr;  // row-pass output: Kc columns of nxy complex values (column-major)
   size_t F1_bytes = 0;
   void* Gw = nullptr;  // pruned spectrum window as node pairs (nrw x (Kc-1) x 2 complex)
   size_t Gw_bytes = 0;

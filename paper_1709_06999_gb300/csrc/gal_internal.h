@@ -76,7 +76,7 @@ struct BatchItem {
   double S;            // N * dxy
   const double* rho2;  // device: squared uv extent of the observation
   int Kc, nrw;         // kept window (same rule as the kernels' bounds)
-  void* F1;            // workspace: N x Kc complex
+  void* F1;            // workspace: Kc columns of N complex values
   void* Gw;            // workspace: the window, nrw x Kc complex (+16 B)
   GatherParams gp;
   const void *u, *v, *re, *im, *w;

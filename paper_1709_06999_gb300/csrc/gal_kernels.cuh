@@ -178,9 +178,10 @@ __global__ void sweep_kernel(const T* __restrict__ I, SweepT<T> p, int N, T* __r
 // ---------------------------------------------------------------------------
 // Row pass.  F1 row i' (i' = 0..N-1) is the real-to-complex FFT of row i' of
 // fftshift(image), i.e. of image row (i' + N/2) mod N with its two halves
-// swapped; only the first Kc output bins are stored (pitch Kc).  The real row
-// x is read as the complex sequence z_n = x_{2n} + i x_{2n+1} (M = N/2
-// points), transformed, and unpacked with
+// swapped; only the first Kc output bins are stored, column-major (column c
+// holds bin c of the N rows).  The real row x is read as the complex
+// sequence z_n = x_{2n} + i x_{2n+1} (M = N/2 points), transformed, and
+// unpacked with
 //   X_k = (Z_k + conj Z_{M-k})/2 - (i/2) W_N^k (Z_k - conj Z_{M-k}).
 // With SWEEP the row is generated from the profile instead of read.
 // ---------------------------------------------------------------------------
@@ -217,7 +218,6 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
   __syncthreads();
   fft_inplace(s, M, t, Tg, tw, 2);
   if (active) {
-    C* out = F1 + (size_t)row * bd.Kc;
     using R = T;
     for (int k = t; k < bd.Kc; k += Tg) {
       const C a = s[k & (M - 1)];
@@ -225,15 +225,15 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
       const C e = mkc((R)0.5 * (a.x + b.x), (R)0.5 * (a.y + b.y));
       const C d = mkc((R)0.5 * (a.x - b.x), (R)0.5 * (a.y - b.y));
       const C o = cmul(cmul_mi(d), __ldg(tw + k));
-      out[k] = cadd(e, o);
+      F1[(size_t)k * N + row] = cadd(e, o);  // column-major: column k holds N rows
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Column pass.  For each kept column c < Kc: complex FFT over the N rows of
-// F1 (pitch Kc), then the v-axis fftshift: output row r holds frequency
-// kv = (r + N/2) mod N.  Only rows r0 .. r0+nrw-1 are kept, written to the
+// F1 (column-major, each column contiguous), then the v-axis fftshift: output
+// row r holds frequency kv = (r + N/2) mod N.  Only rows r0 .. r0+nrw-1 are kept, written to the
 // window Gp[rr Kc + c] (nrw x Kc).  Blocks loop over column groups (grid capped at a few blocks per SM), so a
 // heavily pruned spectrum launches no idle blocks.
 // ---------------------------------------------------------------------------
@@ -251,8 +251,8 @@ col_pass_kernel(const cplx_t<T>* __restrict__ F1, cplx_t<T>* __restrict__ Gp, in
   const int ld = N + 1;  // padded column stride in shared memory
   for (int c0 = blockIdx.x * cpb; c0 < bd.Kc; c0 += gridDim.x * cpb) {
     for (int q = threadIdx.x; q < cpb * N; q += blockDim.x) {
-      const int cl = q % cpb, i = q / cpb, c = c0 + cl;
-      sm[(size_t)cl * ld + i] = c < bd.Kc ? F1[(size_t)i * bd.Kc + c] : mkc((T)0, (T)0);
+      const int i = q % N, cl = q / N, c = c0 + cl;
+      sm[(size_t)cl * ld + i] = c < bd.Kc ? F1[(size_t)c * N + i] : mkc((T)0, (T)0);
     }
     __syncthreads();
     fft_inplace(sm + (size_t)g * ld, N, t, Tg, tw, 1);
@@ -298,7 +298,7 @@ template <typename T, int L, int NSEQ> struct Shape3 {
   static constexpr int RS = (P::padded * (int)sizeof(C) + 15) / 16 * 16 / (int)sizeof(C);
 };
 
-// Row pass: row i' of F1 (pitch Kc) = first Kc bins of the real-to-complex FFT
+// Row pass: row i' of F1 (column-major) = first Kc bins of the real-to-complex FFT
 // of row i' of fftshift(image), i.e. of image row (i' + N/2) mod N with its
 // halves swapped, read as z_n = x_{2n} + i x_{2n+1} (M = N/2 points).
 // TMA: persistent blocks own row groups blockIdx.x + k gridDim.x; thread 0
@@ -309,8 +309,14 @@ template <typename T, int L, int NSEQ> struct Shape3 {
 // copies still in flight (bounded) and ends the block.
 // Otherwise (SWEEP, or an image that is not 16-byte aligned) each block loads
 // or generates its rows directly.
+// at most 128 registers per thread: four 128-thread blocks per SM
+template <int THREADS> constexpr int min_blocks_128regs() {
+  return THREADS >= 512 ? 1 : 512 / THREADS;
+}
+
 template <typename T, int LG, bool TMA, bool SWEEP, int K>
-__global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads)
+__global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads,
+                                  min_blocks_128regs<Shape3<T, (1 << LG), (2 << LG)>::threads>())
 row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
                 int* __restrict__ err) {
   using C = cplx_t<T>;
@@ -345,18 +351,18 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
   auto transform = [&](C (&v)[V], C* A, C* B, int row) {
     Head3<M, V, 2, 0>::run(v, A, B, t, tw, tw1, sync);
     C* in = last_input<M, V>(A, B);
-    C* out = F1 + (size_t)row * bd.Kc;
+    C* out = F1 + row;  // column-major: bin j of this row at out[j N]
     if (pruned) {
       for (int j = t; j < bd.Kc; j += TT) {
         C zj, zmj;
         if (one_j) {
           pruned_pair3<M, V>(in, j, twp, zj, zmj);
-          out[j] = r2c_unpack(zj, zmj, wj);
+          out[(size_t)j * N] = r2c_unpack(zj, zmj, wj);
         } else {
           C tj[V];
           load_twp<M, V, 2>(tj, j, tw);
           pruned_pair3<M, V>(in, j, tj, zj, zmj);
-          out[j] = r2c_unpack(zj, zmj, __ldg(tw + j));
+          out[(size_t)j * N] = r2c_unpack(zj, zmj, __ldg(tw + j));
         }
       }
     } else {
@@ -365,7 +371,8 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       store_full<M, V>(v, o, t);
       __syncthreads();
       for (int k = t; k < bd.Kc; k += TT)
-        out[k] = r2c_unpack(o[pad3<V>(k & (M - 1))], o[pad3<V>((M - k) & (M - 1))], __ldg(tw + k));
+        out[(size_t)k * N] =
+            r2c_unpack(o[pad3<V>(k & (M - 1))], o[pad3<V>((M - k) & (M - 1))], __ldg(tw + k));
     }
   };
   if constexpr (TMA) {
@@ -438,7 +445,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
 }
 
 // Column pass: for each kept column c < Kc (blocks loop over column groups),
-// the complex FFT of length N down column c of F1 (pitch Kc); output row r
+// the complex FFT of length N down column c of F1 (contiguous); output row r
 // of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
 // r0 + nrw - 1 are written to the window Gw (nrw x Kc).  When the window is
 // pruned, only the kept frequencies +-j are evaluated.
@@ -502,7 +509,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
     const bool act = c < bd.Kc;
     C v[V];
 #pragma unroll
-    for (int r = 0; r < V; ++r) v[r] = act ? F1[(size_t)(t + r * TT) * bd.Kc + c] : mkc((T)0, (T)0);
+    for (int r = 0; r < V; ++r) v[r] = act ? F1[(size_t)c * N + t + r * TT] : mkc((T)0, (T)0);
     Head3<N, V, 1, 0>::run(v, A, B, t, tw, tw1, sync);
     C* in = last_input<N, V>(A, B);
     if (pruned) {
@@ -601,7 +608,7 @@ template <typename T> struct RowJob {
   const T* image;       // nxy x nxy image (null when swept from I)
   const T* I;           // profile (SWEEP)
   SweepT<T> sp;
-  cplx_t<T>* F1;        // row-pass output, pitch Kc
+  cplx_t<T>* F1;        // row-pass output, column-major (Kc columns of N)
   const double* rho2;   // squared uv extent of the request's points
   double S;             // nxy * dxy
 };
@@ -1022,7 +1029,12 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
-  for (int64_t q = gtid; q < nq; q += gstride) {
+  // whole grid-stride rounds, then the remaining groups spread over all
+  // blocks (thread t of block b takes group t * gridDim + b), so that no few
+  // blocks run one round more than the rest
+  const int64_t rounds = nq / gstride;
+  const int64_t rem_j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+  auto group = [&](int64_t q) {  // the W points of group q
     T uu[W], vv[W], rr[W], ii[W], ww[W];
     load16(u, q, uu);
     load16(v, q, vv);
@@ -1053,7 +1065,10 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 #pragma unroll
       for (int e = 0; e < W; ++e) vis[q * W + e] = Vs[e];
     }
-  }
+  };
+  int64_t q = gtid;
+  for (int64_t r = 0; r < rounds; ++r, q += gstride) group(q);
+  if (rem_j < nq - rounds * gstride) group(rounds * gstride + rem_j);
   for (int64_t k = nq * W + gtid; k < M; k += gstride) {
     const C V = point(u[k], v[k]);
     if constexpr (CHI2) {
