@@ -73,9 +73,8 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
   const int pf_blocks = p.n > 0 ? 16 : 0;
   Jobs<ColJob<T>, 1> jb;
   jb.j[0] = ColJob<T>{static_cast<const C*>(F1), static_cast<C*>(Gw), rho2, S};
-  kern<<<col_blocks + pf_blocks, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw),
-                                                          col_blocks, p);
-  return cudaGetLastError();
+  return launch_dependent(kern, dim3(col_blocks + pf_blocks), dim3(SH::threads), smem, st, jb,
+                          static_cast<const C*>(tw), col_blocks, p);
 }
 
 template <typename T, int LG>

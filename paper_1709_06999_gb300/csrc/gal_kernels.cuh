@@ -18,6 +18,7 @@
 #include "gal_tma.cuh"
 
 #include <limits>
+#include <utility>
 #include "gal_internal.h"
 
 namespace gal {
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads,
 row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
                 int* __restrict__ err) {
   using C = cplx_t<T>;
+  grid_dep_launch();  // the column pass may be scheduled as our blocks retire
   const RowJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   const T* __restrict__ image = jb.image;
   const T* __restrict__ I = jb.I;
@@ -480,6 +482,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   cplx_t<T>* __restrict__ Gw = jb.Gw;
   const double* __restrict__ rho2 = jb.rho2;
   const double S = jb.S;
+  grid_dep_launch();  // the gather may start its prologue on the SMs we leave idle
   if ((int)blockIdx.x >= col_blocks) {
     l2_prefetch(pf, (blockIdx.x - col_blocks) * blockDim.x + threadIdx.x,
                 (gridDim.x - col_blocks) * blockDim.x);
@@ -504,6 +507,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   C* A = base + (size_t)g * RS;
   C* B = base + (size_t)(G + g) * RS;
   auto sync = [] { __syncthreads(); };
+  grid_dep_wait();  // F1 is the row pass's output
   for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += col_blocks * G) {
     const int c = c0 + g;
     const bool act = c < bd.Kc;
@@ -1106,6 +1110,22 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
   const Bounds bd = block_bounds(rho2, p.Sd, p.N);
   const Window win = make_window(bd, p.N);
   typename Acc<T>::type acc;
+  // the observation does not depend on the column pass: pull this thread's
+  // first group towards L2 while that pass finishes
+  if (vec) {
+    constexpr int W = Vec16<T>::W;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < M / W) {
+      prefetch_l2(u + q * W);
+      prefetch_l2(v + q * W);
+      if constexpr (CHI2) {
+        prefetch_l2(re + q * W);
+        prefetch_l2(im + q * W);
+        prefetch_l2(w + q * W);
+      }
+    }
+  }
+  grid_dep_wait();  // the window is the column pass's output
   if constexpr (SMEM) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     C* sw = reinterpret_cast<C*>(smem_raw);
@@ -1172,6 +1192,25 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+
+// Launch `kern` as a programmatic dependent of the preceding kernel in `st`:
+// it may be scheduled while that kernel finishes, and waits for it in
+// grid_dep_wait() before reading what it wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 namespace gal {
 
 constexpr int kMaxDynSmem = 224 * 1024;  // leaves room for the kernels' static shared memory
@@ -1353,7 +1392,10 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
   Jobs<GatherJob<T>, 1> jb;
   jb.j[0] = GatherJob<T>{g, p, rho2, u, v, re, im, w, M, vec, static_cast<C*>(vis), partials,
                          counter, chi2};
-  auto go = [&](auto kern, size_t smem) { kern<<<grid, threads, smem, st>>>(jb, nodes); };
+  cudaError_t le = cudaSuccess;
+  auto go = [&](auto kern, size_t smem) {
+    le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes);
+  };
   if (chi2) {
     if (window_smem)
       edge ? go(gather_kernel<T, true, true, true, 1>, window_smem)
@@ -1368,6 +1410,7 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
       edge ? go(gather_kernel<T, false, false, true, 1>, 0)
            : go(gather_kernel<T, false, false, false, 1>, 0);
   }
+  if (le != cudaSuccess) return le;
   return cudaGetLastError();
 }
 

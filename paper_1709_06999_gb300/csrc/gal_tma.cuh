@@ -60,4 +60,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may start before the preceding kernel in
+// its stream has finished; grid_dep_wait() blocks until that kernel has
+// completed and its memory operations are visible (a no-op when the kernel
+// was launched normally).  grid_dep_launch() lets the next kernel, if it was
+// launched that way, begin launching; it changes nothing else.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// bring the line holding p into L2 (no register result)
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 }  // namespace gal
