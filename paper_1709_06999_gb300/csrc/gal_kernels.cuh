@@ -560,6 +560,7 @@ struct Window {
   int cmax;   // last cell column, Kc - 2
   int rmax;   // last cell row, nrw - 2
   int rofs;   // N/2 - r0: window row of v = 0
+  unsigned amax;  // node index of the last cell's first node, rmax * pitch + cmax
 };
 __device__ __forceinline__ Window make_window(const Bounds& b, int N) {
   Window w;
@@ -567,6 +568,7 @@ __device__ __forceinline__ Window make_window(const Bounds& b, int N) {
   w.cmax = b.Kc - 2;
   w.rmax = b.nrw - 2;
   w.rofs = N / 2 - b.r0;
+  w.amax = (unsigned)(w.rmax * w.pitch + w.cmax);
   return w;
 }
 
@@ -761,6 +763,15 @@ __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a + b rounded towards minus infinity, both lanes
+__device__ __forceinline__ float2 add2_rd(float2 a, float2 b) {
+  auto pack = [](float2 f) {
+    return ((unsigned long long)__float_as_uint(f.y) << 32) | __float_as_uint(f.x);
+  };
+  unsigned long long r;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack(a)), "l"(pack(b)));
+  return make_float2(__uint_as_float((unsigned)r), __uint_as_float((unsigned)(r >> 32)));
+}
 
 // Round to nearest integer on the FMA pipe: for |x| < 2^22, x + 1.5 2^23
 // rounds x to an integer in the low mantissa bits.  rint_fma(x) is exact there;
@@ -843,6 +854,40 @@ __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const W
   if (neg) V.y = -V.y;
 }
 
+// Both points' cells in a pruned window (no point can reach its edge), from
+// the folded positions x = xh + xl, y = yh + yl (grid offsets, |.| < 2^22):
+// floor(h) + 1.5 2^23 is h + 1.5 2^23 rounded down (one add per lane pair),
+// whose low mantissa bits are the integer floor; the fraction (h - floor h)
+// is exact, plus the low part.  Non-finite input gives an arbitrary node
+// index, clamped so every read stays in the window (its result is NaN
+// through the phase).
+template <bool SMEM>
+__device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, const Window& w,
+                                                 float2 xh, float2 xl, float2 yh, float2 yl,
+                                                 float2 m1, float2& A0, float2& A1) {
+  const float2 mg = make_float2(kMagic, kMagic), nmg = make_float2(-kMagic, -kMagic);
+  const float2 tx = add2_rd(xh, mg), ty = add2_rd(yh, mg);
+  const float2 fu = add2(fma2(add2(tx, nmg), m1, xh), xl);
+  const float2 fv = add2(fma2(add2(ty, nmg), m1, yh), yl);
+  constexpr int kMagicBits = 0x4B400000;  // bit pattern of 1.5 2^23
+  auto node = [&](float t_x, float t_y) {
+    const int r = __float_as_int(t_y) - kMagicBits + w.rofs;
+    const int c = __float_as_int(t_x) - kMagicBits;
+    return min((unsigned)(r * w.pitch + c), w.amax);
+  };
+  auto lerp = [&](unsigned a, float f_u, float f_v) {
+    const float2* g = G + a;
+    const float2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
+    const float2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
+    const float2 FU = pk(f_u, f_u), FV = pk(f_v, f_v);
+    const float2 a0 = fma2(FU, fma2(g00, m1, g01), g00);
+    const float2 b0 = fma2(FU, fma2(g10, m1, g11), g10);
+    return fma2(FV, fma2(a0, m1, b0), a0);
+  };
+  A0 = lerp(node(tx.x, ty.x), fu.x, fv.x);
+  A1 = lerp(node(tx.y, ty.y), fu.y, fv.y);
+}
+
 template <bool SMEM, bool EDGE>
 __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const Window& w,
                                             const Pair2Const& k, float2 U, float2 Vv, float2& V0,
@@ -876,8 +921,14 @@ __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const 
   const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
   const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
   float2 A0, A1;
-  cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
-  cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
+  if constexpr (EDGE) {
+    cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
+    cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
+  } else {
+    cell_pair_pruned<SMEM>(G, w, xh, xl, yh, yl, k.m1, A0, A1);
+    if (n0) A0.y = -A0.y;
+    if (n1) A1.y = -A1.y;
+  }
   // rotate by the phase: V (c + i s) = c V + s (-Vi, Vr)
   V0 = fma2(pk(s0, s0), pk(-A0.y, A0.x), mul2(pk(c0, c0), A0));
   V1 = fma2(pk(s1, s1), pk(-A1.y, A1.x), mul2(pk(c1, c1), A1));
