@@ -107,6 +107,20 @@ int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const floa
                         const float* im, const float* w, int64_t M, void* stream, gal_data** out);
 int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
                         const double* im, const double* w, int64_t M, void* stream, gal_data** out);
+/* Register an observation whose baselines u_m, v_m are in metres, with the
+ * frequency nu (Hz) of every visibility (lifts the single-frequency assumption
+ * of Sect. 3: each visibility samples the model at its own u_m nu / c).  The
+ * wavelengths u = u_m nu / c, v = v_m nu / c are computed once, in FP64 and
+ * rounded to the precision, into device arrays the handle owns (2 M values,
+ * freed by gal_data_destroy); u_m, v_m, nu are not used after the call returns.
+ * re, im, w are borrowed as in gal_data_create_*.  Same errors, plus
+ * GAL_E_NOMEM if the owned arrays cannot be allocated. */
+int gal_data_create_freq_f32(gal_ctx* ctx, const float* u_m, const float* v_m, const float* nu,
+                             const float* re, const float* im, const float* w, int64_t M,
+                             void* stream, gal_data** out);
+int gal_data_create_freq_f64(gal_ctx* ctx, const double* u_m, const double* v_m,
+                             const double* nu, const double* re, const double* im,
+                             const double* w, int64_t M, void* stream, gal_data** out);
 /* Release a handle (not the borrowed arrays).  Waits for the device. */
 void gal_data_destroy(gal_data* data);
 /* Number of visibilities and bytes per real value (4 or 8) of a handle. */

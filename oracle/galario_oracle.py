@@ -39,6 +39,7 @@ __all__ = [
     "rotate_uv",
     "uv_to_index",
     "image_size",
+    "uv_from_frequency",
     "bilinear",
     "sample_spectrum",
     "sample_image",
@@ -284,3 +285,18 @@ def image_size(u, v, PB: float = 0.0, f_min: float = 5.0, f_max: float = 2.5):
     mant, expo = math.frexp(need)                 # need = mant * 2**expo, mant in [0.5, 1)
     nxy = 2 ** (expo - 1) if mant == 0.5 else 2 ** expo
     return int(nxy), 1.0 / (nxy * duv)
+
+
+SPEED_OF_LIGHT = 299792458.0  # m/s, exact by the SI definition of the metre
+
+
+def uv_from_frequency(u_m, v_m, nu):
+    """Baselines in metres observed at frequency nu (Hz) expressed in
+    wavelengths, u = u_m nu / c (Sect. 3: uv coordinates are baselines in
+    units of the observing wavelength).  With one nu per visibility the
+    single-frequency assumption of Sect. 3 is lifted: each visibility samples
+    the model at its own uv.  Computed as (u_m nu) / c."""
+    u_m = np.asarray(u_m, dtype=np.float64)
+    v_m = np.asarray(v_m, dtype=np.float64)
+    nu = np.asarray(nu, dtype=np.float64)
+    return (u_m * nu) / SPEED_OF_LIGHT, (v_m * nu) / SPEED_OF_LIGHT

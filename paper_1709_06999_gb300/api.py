@@ -133,20 +133,26 @@ class Observation:
     alive.  Creation enqueues one reduction for the uv extent.
     """
 
-    def __init__(self, ctx: "Context", u, v, re, im, w):
-        tensors = [ctx._dev(t) for t in (u, v, re, im, w)]
+    def __init__(self, ctx: "Context", u, v, re, im, w, nu=None):
+        """u, v in wavelengths; or, with `nu` (Hz per visibility), in metres
+        (gal_data_create_freq_*: the library converts them once)."""
+        arrays = (u, v, re, im, w) if nu is None else (u, v, nu, re, im, w)
+        tensors = [ctx._dev(t).contiguous() for t in arrays]
         m = tensors[0].numel()
         if any(t.numel() != m for t in tensors):
-            raise ValueError("u, v, re, im, w must have the same length")
-        self._tensors = tensors
+            raise ValueError("u, v, re, im, w (and nu) must have the same length")
         self.ctx = ctx
         self.M = m
         self.dtype = tensors[0].dtype
         sfx = _suffix(*tensors)
         h = ct.c_void_p()
-        fn = getattr(ctx.lib, f"gal_data_create_{sfx}")
+        name = f"gal_data_create_{sfx}" if nu is None else f"gal_data_create_freq_{sfx}"
+        fn = getattr(ctx.lib, name)
         _check(ctx.handle, fn(ctx.handle, *[t.data_ptr() for t in tensors], m, ctx._stream(), ct.byref(h)))
         self.handle = h
+        # borrowed arrays stay alive with the handle (with nu, u and v live in
+        # the library)
+        self._tensors = tensors if nu is None else tensors[3:]
 
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
@@ -215,6 +221,10 @@ class Context:
         n = (ct.c_int64 * 4)()
         _check(self.handle, self.lib.gal_stage_times(self.handle, ms, n))
         return [(ms[i], n[i]) for i in range(4)]
+
+    def register_freq(self, u_m, v_m, nu, re, im, w) -> Observation:
+        """Register visibilities with baselines in metres and their frequencies (Hz)."""
+        return Observation(self, u_m, v_m, re, im, w, nu=nu)
 
     def register(self, u, v, re, im, w) -> Observation:
         return Observation(self, u, v, re, im, w)

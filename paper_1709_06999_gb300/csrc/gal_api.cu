@@ -82,6 +82,7 @@ struct gal_data {
   const void *u = nullptr, *v = nullptr, *re = nullptr, *im = nullptr, *w = nullptr;
   double* rho2 = nullptr;  // device scalar: max(u^2 + v^2)
   double rho2_host = 0.0;  // the same value, read back once at registration
+  void* uv_own = nullptr;  // u, v in wavelengths when registered from metres (2 M values)
 };
 
 namespace {
@@ -429,6 +430,38 @@ int data_create_t(gal_ctx* ctx, const T* u, const T* v, const T* re, const T* im
   *out = d;
   return GAL_OK;
 }
+
+// Registration from baselines in metres and one frequency per visibility:
+// u, v in wavelengths (u_m nu / c) are computed once into arrays the handle
+// owns, then the observation is registered as usual.
+template <typename T>
+int data_create_freq_t(gal_ctx* ctx, const T* u_m, const T* v_m, const T* nu, const T* re,
+                       const T* im, const T* w, int64_t M, void* stream, gal_data** out) {
+  if (!ctx || !out || M < 0) return GAL_E_INVAL;
+  if (M > 0 && (!u_m || !v_m || !nu)) return GAL_E_INVAL;
+  for (const void* p : {(const void*)u_m, (const void*)v_m, (const void*)nu})
+    if (!aligned(p, sizeof(T))) return GAL_E_INVAL;
+  void* own = nullptr;
+  if (M > 0) GAL_CUDA(ctx, cudaMalloc(&own, 2 * sizeof(T) * (size_t)M + 16));
+  T* u = static_cast<T*>(own);
+  // v starts 16-byte aligned so the gather can read both as vectors
+  T* v = u ? reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(u + M) + 15) & ~uintptr_t(15))
+           : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int s = GAL_OK;
+  if (M > 0)
+    s = stage(ctx, 0, st, [&] {
+      return gal::Launch<T>::uv_from_frequency(u_m, v_m, nu, M, u, v, ctx->aux_blocks, st);
+    });
+  if (s == GAL_OK) s = data_create_t<T>(ctx, u, v, re, im, w, M, stream, out);
+  if (s != GAL_OK) {
+    if (own) cudaFree(own);
+    return s;
+  }
+  (*out)->uv_own = own;
+  return GAL_OK;
+}
+
 
 template <typename T>
 int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, double dRA,
@@ -1028,6 +1061,17 @@ int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const do
                         gal_data** out) {
   return data_create_t<double>(ctx, u, v, re, im, w, M, stream, out);
 }
+int gal_data_create_freq_f32(gal_ctx* ctx, const float* u_m, const float* v_m, const float* nu,
+                             const float* re, const float* im, const float* w, int64_t M,
+                             void* stream, gal_data** out) {
+  return data_create_freq_t<float>(ctx, u_m, v_m, nu, re, im, w, M, stream, out);
+}
+int gal_data_create_freq_f64(gal_ctx* ctx, const double* u_m, const double* v_m,
+                             const double* nu, const double* re, const double* im,
+                             const double* w, int64_t M, void* stream, gal_data** out) {
+  return data_create_freq_t<double>(ctx, u_m, v_m, nu, re, im, w, M, stream, out);
+}
+
 int gal_data_info(const gal_data* d, int64_t* M_out, int* real_bytes_out) {
   if (!d) return GAL_E_INVAL;
   if (M_out) *M_out = d->M;
@@ -1039,6 +1083,7 @@ void gal_data_destroy(gal_data* d) {
   if (!d) return;
   cudaDeviceSynchronize();
   if (d->rho2) cudaFree(d->rho2);
+  if (d->uv_own) cudaFree(d->uv_own);
   delete d;
 }
 

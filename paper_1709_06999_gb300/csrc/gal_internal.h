@@ -41,6 +41,10 @@ template <typename T> struct Launch {
   static cudaError_t twiddles(void* tw, int N, cudaStream_t st);
   static cudaError_t extent(const T* u, const T* v, int64_t M, double* rho2, int blocks,
                             cudaStream_t st);
+  // u = u_m nu / c, v = v_m nu / c (metres and Hz to wavelengths), in FP64,
+  // rounded once to T
+  static cudaError_t uv_from_frequency(const T* u_m, const T* v_m, const T* nu, int64_t M, T* u,
+                                       T* v, int blocks, cudaStream_t st);
   // range2[0] = min_k, range2[1] = max_k of u_k^2 + v_k^2 (finite points)
   static cudaError_t uv_range(const T* u, const T* v, int64_t M, double* range2, int blocks,
                               cudaStream_t st);

@@ -72,6 +72,22 @@ __global__ void extent_kernel(const T* __restrict__ u, const T* __restrict__ v, 
   }
 }
 
+// u_k = u_m,k nu_k / c and the same for v: baselines in metres at each
+// visibility's own frequency, in wavelengths (Sect. 3, the frequency
+// assumption lifted).  FP64 product then quotient, rounded to T once.
+template <typename T>
+__global__ void uv_from_frequency_kernel(const T* __restrict__ u_m, const T* __restrict__ v_m,
+                                         const T* __restrict__ nu, int64_t M, T* __restrict__ u,
+                                         T* __restrict__ v) {
+  constexpr double kC = 299792458.0;  // m / s, exact by the definition of the metre
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double f = (double)nu[k];
+    u[k] = (T)(__dmul_rn((double)u_m[k], f) / kC);  // (u_m nu) / c, each step rounded once
+    v[k] = (T)(__dmul_rn((double)v_m[k], f) / kC);
+  }
+}
+
 // min_k and max_k of u_k^2 + v_k^2 over the finite points (Sect. 3.3, criteria
 // (i) and (iia)); range2[0] must start at +inf and range2[1] at 0.  Non-negative
 // doubles order like their bit patterns, so the block results are combined
@@ -1341,6 +1357,16 @@ cudaError_t Launch<T>::extent(const T* u, const T* v, int64_t M, double* rho2, i
   const int64_t need = (M + 255) / 256;
   const int grid = (int)(need < blocks ? need : blocks);
   extent_kernel<T><<<grid, 256, 0, st>>>(u, v, M, rho2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::uv_from_frequency(const T* u_m, const T* v_m, const T* nu, int64_t M, T* u,
+                                         T* v, int blocks, cudaStream_t st) {
+  if (M <= 0) return cudaSuccess;
+  const int64_t need = (M + 255) / 256;
+  const int grid = (int)(need < blocks ? need : blocks);
+  uv_from_frequency_kernel<T><<<grid, 256, 0, st>>>(u_m, v_m, nu, M, u, v);
   return cudaGetLastError();
 }
 

@@ -80,15 +80,17 @@ def noise(w: np.ndarray, seed) -> tuple[np.ndarray, np.ndarray]:
 
 def alma_like_uv(M: int, seed, n_ant: int = 43, r_min_m: float = 15.0, r_max_m: float = 3000.0,
                  lat: float = -23.0 * DEG, dec: float = -35.0 * DEG, ha_hours: float = 2.0,
-                 n_time: int = 60, freq0_hz: float = 100e9, half_band_hz: float = 3.75e9
-                 ) -> tuple[np.ndarray, np.ndarray]:
+                 n_time: int = 60, freq0_hz: float = 100e9, half_band_hz: float = 3.75e9,
+                 metres: bool = False):
     """ALMA-like Earth-rotation tracks, truncated to exactly M points.
 
     ``n_ant`` antennas at log-uniform radius in [r_min_m, r_max_m] and uniform
     azimuth on a flat site at latitude ``lat``; baselines are projected with
     the standard (X, Y, Z) -> (u, v) transform for hour angles uniformly in
     [-ha, +ha] (n_time steps) and declination ``dec``; channels spread over
-    freq0 +- half_band are added until M points exist.
+    freq0 +- half_band are added until M points exist.  Returns (u, v) in
+    wavelengths, or with ``metres`` the baselines in metres and each point's
+    frequency in Hz, (u_m, v_m, nu).
     """
     rng = _rng(seed)
     rad = np.exp(rng.uniform(math.log(r_min_m), math.log(r_max_m), n_ant))
@@ -107,6 +109,11 @@ def alma_like_uv(M: int, seed, n_ant: int = 43, r_min_m: float = 15.0, r_max_m: 
     per_chan = u_m.size
     n_chan = max(1, -(-M // per_chan))
     freqs = freq0_hz + (np.linspace(-half_band_hz, half_band_hz, n_chan) if n_chan > 1 else np.zeros(1))
+    if metres:
+        um = np.broadcast_to(u_m[None, :], (n_chan, per_chan)).ravel()[:M].copy()
+        vm = np.broadcast_to(v_m[None, :], (n_chan, per_chan)).ravel()[:M].copy()
+        nu = np.broadcast_to(freqs[:, None], (n_chan, per_chan)).ravel()[:M].copy()
+        return um, vm, nu
     c_light = 299792458.0
     scale = freqs / c_light
     u = (u_m[None, :] * scale[:, None]).ravel()[:M]

@@ -394,6 +394,16 @@ def check_image_size_table(O):
         assert n == int(n2)
 
 
+def check_uv_from_frequency(O):
+    """Metres to wavelengths: a 1 km baseline at c / 1 mm = 299.792458 GHz is
+    exactly 1e6 wavelengths; 15 m at 100 GHz is 5003.461 wavelengths; the
+    conversion is linear in both factors."""
+    u, v = O.uv_from_frequency([1000.0, 15.0], [-500.0, 0.0], [299792458000.0, 100e9])
+    assert u[0] == 1e6 and v[0] == -5e5
+    assert abs(u[1] - 15.0 * 100e9 / 299792458.0) < 1e-9 and v[1] == 0.0
+    assert abs(u[1] - 5003.461) < 1e-3
+
+
 ALL_CHECKS = [
     check_half_spectrum_bruteforce,
     check_sample_nodes_bruteforce,
@@ -411,4 +421,5 @@ ALL_CHECKS = [
     check_linearity,
     check_sweep_pixels,
     check_image_size_table,
+    check_uv_from_frequency,
 ]

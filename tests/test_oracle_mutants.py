@@ -44,6 +44,8 @@ MUTANTS = {
     "size_no_f_max": ("need = 2.0 * f_max * rho_max / duv", "need = 2.0 * rho_max / duv"),
     "size_iib_alone": ("duv = min(duv, 1.0 / PB)", "duv = 1.0 / PB"),
     "size_round_down": ("nxy = 2 ** (expo - 1) if mant == 0.5 else 2 ** expo", "nxy = 2 ** (expo - 1)"),
+    "freq_wavelength_inverted": ("return (u_m * nu) / SPEED_OF_LIGHT, (v_m * nu) / SPEED_OF_LIGHT",
+                                 "return (u_m / nu) * SPEED_OF_LIGHT, (v_m / nu) * SPEED_OF_LIGHT"),
     "size_pixel_from_extent": ("return int(nxy), 1.0 / (nxy * duv)",
                                "return int(nxy), 1.0 / (2.0 * f_max * rho_max)"),
 }
