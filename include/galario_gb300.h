@@ -193,6 +193,45 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
                             double dRA, double dDec, double PA, const gal_data* data,
                             double* chi2_host, void* stream);
 
+/* ---- multi-source composition --------------------------------------------------------- */
+
+/* Largest number of copies in one multi-source call. */
+#define GAL_MAX_SOURCES 16
+
+/* Visibilities (and chi-square) of K copies of one model: copy k scaled by
+ * amp[k] and displaced by (dRA[k], dDec[k]) radians, all rotated by PA (end of
+ * Sect. 3.1: by the linearity of the Fourier transform, identical sources at
+ * different places need one transform; each is displaced by its own phase,
+ * Sect. 3.2).  The sampled model visibility is multiplied by
+ *   sum_k amp[k] exp(+2 pi i (u dRA[k] + v dDec[k]))
+ * instead of one phase factor: one FFT and one interpolation per uv point
+ * serve all K copies.  dRA, dDec, amp: K host doubles, K in [1, GAL_MAX_SOURCES]
+ * (GAL_E_INVAL otherwise or for non-finite values); with K = 1 and amp = 1
+ * the result is bitwise that of the single-offset call.  Other arguments as in
+ * the single-source calls. */
+int gal_sample_image_multi_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double PA,
+                               int K, const double* dRA, const double* dDec, const double* amp,
+                               int64_t M, const float* u, const float* v, float* vis_out,
+                               void* stream);
+int gal_sample_image_multi_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double PA,
+                               int K, const double* dRA, const double* dDec, const double* amp,
+                               int64_t M, const double* u, const double* v, double* vis_out,
+                               void* stream);
+int gal_chi2_image_multi_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double PA,
+                             int K, const double* dRA, const double* dDec, const double* amp,
+                             const gal_data* data, double* chi2_out, void* stream);
+int gal_chi2_image_multi_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double PA,
+                             int K, const double* dRA, const double* dDec, const double* amp,
+                             const gal_data* data, double* chi2_out, void* stream);
+int gal_chi2_profile_multi_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR,
+                               int nxy, double dxy, double inc, double PA, int K,
+                               const double* dRA, const double* dDec, const double* amp,
+                               const gal_data* data, double* chi2_out, void* stream);
+int gal_chi2_profile_multi_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR,
+                               int nxy, double dxy, double inc, double PA, int K,
+                               const double* dRA, const double* dDec, const double* amp,
+                               const gal_data* data, double* chi2_out, void* stream);
+
 /* ---- batches ------------------------------------------------------------------------- */
 
 /* One chi-square request of a batch: chi2Image when `image` is set, chi2Profile

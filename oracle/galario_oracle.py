@@ -40,6 +40,9 @@ __all__ = [
     "uv_to_index",
     "image_size",
     "uv_from_frequency",
+    "sample_image_multi",
+    "chi2_image_multi",
+    "chi2_profile_multi",
     "bilinear",
     "sample_spectrum",
     "sample_image",
@@ -300,3 +303,28 @@ def uv_from_frequency(u_m, v_m, nu):
     v_m = np.asarray(v_m, dtype=np.float64)
     nu = np.asarray(nu, dtype=np.float64)
     return (u_m * nu) / SPEED_OF_LIGHT, (v_m * nu) / SPEED_OF_LIGHT
+
+
+def sample_image_multi(image, dxy: float, u, v, dRA, dDec, amp=None, PA: float = 0.0):
+    """K copies of one model at different places (end of Sect. 3.1): by
+    linearity of the Fourier transform, the sum over k of amp[k] times the
+    visibilities of the model displaced by (dRA[k], dDec[k]) (Sect. 3.2), all
+    rotated by PA."""
+    amp = [1.0] * len(dRA) if amp is None else amp
+    total = 0.0
+    for a, x, y in zip(amp, dRA, dDec):
+        total = total + a * sample_image(image, dxy, u, v, x, y, PA)
+    return total
+
+
+def chi2_image_multi(image, dxy: float, u, v, re_obs, im_obs, w, dRA, dDec, amp=None,
+                     PA: float = 0.0):
+    """chi-square (Sect. 3.1) of the multi-source model of sample_image_multi."""
+    return chi2(sample_image_multi(image, dxy, u, v, dRA, dDec, amp, PA), re_obs, im_obs, w)
+
+
+def chi2_profile_multi(intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v, re_obs,
+                       im_obs, w, dRA, dDec, amp=None, PA: float = 0.0, inc: float = 0.0):
+    """chi-square of K copies of the swept profile (sweep, then sample_image_multi)."""
+    img = sweep(intensity, Rmin, dR, nxy, dxy, inc)
+    return chi2_image_multi(img, dxy, u, v, re_obs, im_obs, w, dRA, dDec, amp, PA)

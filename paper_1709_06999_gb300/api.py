@@ -308,6 +308,57 @@ class Context:
                                obs.handle, ct.byref(res), self._stream()))
         return res.value
 
+    # -- multi-source composition (K offset copies of one model) -------------
+    @staticmethod
+    def _sources(dRA, dDec, amp):
+        dRA = [float(x) for x in dRA]
+        dDec = [float(x) for x in dDec]
+        amp = [1.0] * len(dRA) if amp is None else [float(x) for x in amp]
+        if not (len(dRA) == len(dDec) == len(amp)):
+            raise ValueError("dRA, dDec and amp must have the same length")
+        arr = lambda xs: (ct.c_double * max(1, len(xs)))(*xs)  # noqa: E731
+        return len(dRA), arr(dRA), arr(dDec), arr(amp)
+
+    def sample_image_multi(self, image, dxy: float, u, v, dRA, dDec, amp=None, PA: float = 0.0,
+                           out=None):
+        """Visibilities of K copies of `image`, copy k scaled by amp[k] and
+        shifted by (dRA[k], dDec[k]), all rotated by PA: one FFT for all."""
+        img, u, v = self._dev(image), self._dev(u), self._dev(v)
+        sfx = _suffix(img, u, v)
+        K, a, b, c = self._sources(dRA, dDec, amp)
+        m = u.numel()
+        if out is None:
+            out = torch.empty((m, 2), dtype=img.dtype, device=self.device)
+        fn = getattr(self.lib, f"gal_sample_image_multi_{sfx}")
+        _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, PA, K, a, b, c, m,
+                               u.data_ptr(), v.data_ptr(), out.data_ptr(), self._stream()))
+        return out
+
+    def chi2_image_multi(self, image, dxy: float, obs: Observation, dRA, dDec, amp=None,
+                         PA: float = 0.0, out=None):
+        img = self._dev(image)
+        sfx = _suffix(img)
+        K, a, b, c = self._sources(dRA, dDec, amp)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        fn = getattr(self.lib, f"gal_chi2_image_multi_{sfx}")
+        _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, PA, K, a, b, c,
+                               obs.handle, out.data_ptr(), self._stream()))
+        return out
+
+    def chi2_profile_multi(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float,
+                           obs: Observation, dRA, dDec, amp=None, inc: float = 0.0,
+                           PA: float = 0.0, out=None):
+        I = self._dev(intensity)
+        sfx = _suffix(I)
+        K, a, b, c = self._sources(dRA, dDec, amp)
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        fn = getattr(self.lib, f"gal_chi2_profile_multi_{sfx}")
+        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc, PA,
+                               K, a, b, c, obs.handle, out.data_ptr(), self._stream()))
+        return out
+
     def chi2_batch(self, requests, out=None):
         """chi-square of every Request, as a float64 tensor of len(requests)
         (gal_chi2_batch: shared launches per pass and image side)."""

@@ -259,7 +259,8 @@ int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& s
 template <typename T>
 int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
                 double dxy, double dRA, double dDec, double PA, int64_t M, const T* u,
-                const T* v, T* vis, cudaStream_t st) {
+                const T* v, T* vis, cudaStream_t st,
+                const gal::MultiSources* ms = nullptr) {
   if (!ctx) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
   if (M < 0) return GAL_E_INVAL;
@@ -276,7 +277,7 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   const int blocks = ctx->gather_blocks[prec_index<T>()][0];
   return stage(ctx, 3, st, [&] {
     return gal::Launch<T>::gather(ctx->Gw, gp, ctx->rho2, u, v, nullptr, nullptr, nullptr, M,
-                                  vis, nullptr, nullptr, nullptr, 0, true, blocks, st);
+                                  vis, nullptr, nullptr, nullptr, 0, true, blocks, ms, st);
   });
 }
 
@@ -306,7 +307,7 @@ template <typename T> int chi2_gather_shape(gal_ctx* ctx, const gal::Bounds& bd,
 template <typename T>
 int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
               double dxy, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
-              cudaStream_t st) {
+              cudaStream_t st, const gal::MultiSources* ms = nullptr) {
   if (!ctx || !d || !chi2) return GAL_E_INVAL;
   if (d->device != ctx->device || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
@@ -328,7 +329,7 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
                                   static_cast<const T*>(d->v), static_cast<const T*>(d->re),
                                   static_cast<const T*>(d->im), static_cast<const T*>(d->w), d->M,
                                   nullptr, ctx->partials, ctx->counter, chi2, wbytes,
-                                  /*edge=*/bd.r0 == 0, blocks, st);
+                                  /*edge=*/bd.r0 == 0, blocks, ms, st);
   });
 }
 
@@ -370,6 +371,37 @@ int chi2_profile_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int
   gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
   return chi2_impl<T>(ctx, nullptr, I, sp, nxy, dxy, dRA, dDec, PA, d, chi2,
                       static_cast<cudaStream_t>(stream));
+}
+
+// Multi-source arguments: K in [1, 16] finite offsets and amplitudes (host).
+int check_multi(int K, const double* dRA, const double* dDec, const double* amp) {
+  if (K < 1 || K > 16 || !dRA || !dDec || !amp) return GAL_E_INVAL;
+  for (int k = 0; k < K; ++k)
+    if (!std::isfinite(dRA[k]) || !std::isfinite(dDec[k]) || !std::isfinite(amp[k]))
+      return GAL_E_INVAL;
+  return GAL_OK;
+}
+
+template <typename T>
+int sample_image_multi_t(gal_ctx* ctx, const T* image, int nxy, double dxy, double PA, int K,
+                         const double* dRA, const double* dDec, const double* amp, int64_t M,
+                         const T* u, const T* v, T* vis, void* stream) {
+  if (!image || !aligned(image, 2 * sizeof(T))) return GAL_E_INVAL;
+  GAL_TRY(check_multi(K, dRA, dDec, amp));
+  const gal::MultiSources ms{K, dRA, dDec, amp};
+  gal::SweepParams sp{};
+  return sample_impl<T>(ctx, image, nullptr, sp, nxy, dxy, 0.0, 0.0, PA, M, u, v, vis,
+                        static_cast<cudaStream_t>(stream), &ms);
+}
+
+template <typename T>
+int chi2_multi_t(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
+                 double dxy, double PA, int K, const double* dRA, const double* dDec,
+                 const double* amp, const gal_data* d, double* chi2, void* stream) {
+  GAL_TRY(check_multi(K, dRA, dDec, amp));
+  const gal::MultiSources ms{K, dRA, dDec, amp};
+  return chi2_impl<T>(ctx, image, I, sp, nxy, dxy, 0.0, 0.0, PA, d, chi2,
+                      static_cast<cudaStream_t>(stream), &ms);
 }
 
 template <typename T>
@@ -1070,6 +1102,53 @@ int gal_data_create_freq_f64(gal_ctx* ctx, const double* u_m, const double* v_m,
                              const double* nu, const double* re, const double* im,
                              const double* w, int64_t M, void* stream, gal_data** out) {
   return data_create_freq_t<double>(ctx, u_m, v_m, nu, re, im, w, M, stream, out);
+}
+
+int gal_sample_image_multi_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double PA,
+                               int K, const double* dRA, const double* dDec, const double* amp,
+                               int64_t M, const float* u, const float* v, float* vis_out,
+                               void* stream) {
+  return sample_image_multi_t<float>(ctx, image, nxy, dxy, PA, K, dRA, dDec, amp, M, u, v,
+                                     vis_out, stream);
+}
+int gal_sample_image_multi_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double PA,
+                               int K, const double* dRA, const double* dDec, const double* amp,
+                               int64_t M, const double* u, const double* v, double* vis_out,
+                               void* stream) {
+  return sample_image_multi_t<double>(ctx, image, nxy, dxy, PA, K, dRA, dDec, amp, M, u, v,
+                                      vis_out, stream);
+}
+int gal_chi2_image_multi_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double PA,
+                             int K, const double* dRA, const double* dDec, const double* amp,
+                             const gal_data* data, double* chi2_out, void* stream) {
+  if (!image || !aligned(image, 8)) return GAL_E_INVAL;
+  return chi2_multi_t<float>(ctx, image, nullptr, gal::SweepParams{}, nxy, dxy, PA, K, dRA, dDec,
+                             amp, data, chi2_out, stream);
+}
+int gal_chi2_image_multi_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double PA,
+                             int K, const double* dRA, const double* dDec, const double* amp,
+                             const gal_data* data, double* chi2_out, void* stream) {
+  if (!image || !aligned(image, 16)) return GAL_E_INVAL;
+  return chi2_multi_t<double>(ctx, image, nullptr, gal::SweepParams{}, nxy, dxy, PA, K, dRA,
+                              dDec, amp, data, chi2_out, stream);
+}
+int gal_chi2_profile_multi_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR,
+                               int nxy, double dxy, double inc, double PA, int K,
+                               const double* dRA, const double* dDec, const double* amp,
+                               const gal_data* data, double* chi2_out, void* stream) {
+  GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
+  if (!aligned(I, sizeof(float))) return GAL_E_INVAL;
+  return chi2_multi_t<float>(ctx, nullptr, I, gal::SweepParams{Rmin, dR, dxy, inc, nr}, nxy, dxy,
+                             PA, K, dRA, dDec, amp, data, chi2_out, stream);
+}
+int gal_chi2_profile_multi_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR,
+                               int nxy, double dxy, double inc, double PA, int K,
+                               const double* dRA, const double* dDec, const double* amp,
+                               const gal_data* data, double* chi2_out, void* stream) {
+  GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
+  if (!aligned(I, sizeof(double))) return GAL_E_INVAL;
+  return chi2_multi_t<double>(ctx, nullptr, I, gal::SweepParams{Rmin, dR, dxy, inc, nr}, nxy,
+                              dxy, PA, K, dRA, dDec, amp, data, chi2_out, stream);
 }
 
 int gal_data_info(const gal_data* d, int64_t* M_out, int* real_bytes_out) {

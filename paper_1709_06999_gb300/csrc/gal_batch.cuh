@@ -111,7 +111,7 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
   const int threads = gather_threads<SMEM>();
-  kern<<<dim3(grid, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)));
+  kern<<<dim3(grid, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
   return cudaGetLastError();
 }
 

@@ -6,21 +6,6 @@
 
 namespace gal {
 
-// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
-// the current device (the attribute is per device; set once per size).
-template <auto Kern> cudaError_t ensure_smem_attr(size_t smem) {
-  constexpr int kDev = 64;
-  static size_t done[kDev] = {};
-  if (smem <= 48 * 1024) return cudaSuccess;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e) return e;
-  if (dev >= 0 && dev < kDev && done[dev] >= smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && dev >= 0 && dev < kDev) done[dev] = smem;
-  return e;
-}
-
 template <typename T, int LG, bool SWEEP>
 cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const void* tw,
                         void* F1, const double* rho2, double S, int* err, cudaStream_t st) {

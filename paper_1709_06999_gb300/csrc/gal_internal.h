@@ -30,6 +30,15 @@ struct L2Prefetch {
   int n;
 };
 
+// K offset copies of one model (multi-source composition): host arrays of
+// K offsets (radians) and amplitudes, K in [1, 16].
+struct MultiSources {
+  int K;
+  const double* dRA;
+  const double* dDec;
+  const double* amp;
+};
+
 // Host launchers, one explicit instantiation per precision.
 template <typename T> struct Launch {
   static cudaError_t init();  // kernel attributes; once per process
@@ -59,11 +68,12 @@ template <typename T> struct Launch {
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
                               const double* rho2, double S, int kc_hint, const L2Prefetch* pf,
                               cudaStream_t st);
+  // ms: multi-source offsets (null: the single offset of gp)
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
                             int64_t M, void* vis, double* partials, unsigned* counter,
                             double* chi2, size_t window_smem, bool edge, int blocks,
-                            cudaStream_t st);
+                            const MultiSources* ms, cudaStream_t st);
 };
 
 // Requests per launch of the batched passes (their job arrays are kernel

@@ -18,6 +18,7 @@
 #include "gal_tma.cuh"
 
 #include <limits>
+#include <type_traits>
 #include <utility>
 #include "gal_internal.h"
 
@@ -671,6 +672,60 @@ template <typename T> struct GatherJob {
   double* chi2_out;
 };
 
+// Offsets and amplitudes of the K copies of one model in a multi-source
+// evaluation (end of Sect. 3.1): the sampled model visibility is multiplied by
+// sum_k amp_k exp(+2 pi i (u dRA_k + v dDec_k)) instead of one phase factor.
+constexpr int kMaxSources = 16;
+template <typename T> struct MultiPhase;
+template <> struct MultiPhase<float> {
+  int K = 0;
+  float2 PXh[kMaxSources], PXl[kMaxSources], PYh[kMaxSources], PYl[kMaxSources];  // broadcast
+  float2 amp[kMaxSources];                                                      // broadcast
+  float PXs[kMaxSources], PXsl[kMaxSources], PYs[kMaxSources], PYsl[kMaxSources];  // scalar
+  float amps[kMaxSources];
+  __host__ static MultiPhase make(int K, const double* dRA, const double* dDec, const double* a) {
+    MultiPhase m;
+    m.K = K;
+    for (int k = 0; k < K; ++k) {
+      const ff x = ff_split(dRA[k]), y = ff_split(dDec[k]);
+      m.PXh[k] = make_float2(x.hi, x.hi);
+      m.PXl[k] = make_float2(x.lo, x.lo);
+      m.PYh[k] = make_float2(y.hi, y.hi);
+      m.PYl[k] = make_float2(y.lo, y.lo);
+      m.amp[k] = make_float2((float)a[k], (float)a[k]);
+      m.PXs[k] = x.hi;
+      m.PXsl[k] = x.lo;
+      m.PYs[k] = y.hi;
+      m.PYsl[k] = y.lo;
+      m.amps[k] = (float)a[k];
+    }
+    return m;
+  }
+};
+template <> struct MultiPhase<double> {
+  int K = 0;
+  double phx[kMaxSources], phy[kMaxSources], amp[kMaxSources];
+  __host__ static MultiPhase make(int K, const double* dRA, const double* dDec, const double* a) {
+    MultiPhase m;
+    m.K = K;
+    for (int k = 0; k < K; ++k) {
+      m.phx[k] = dRA[k];
+      m.phy[k] = dDec[k];
+      m.amp[k] = a[k];
+    }
+    return m;
+  }
+};
+
+// the gather's multi-source parameter: empty unless MULTI
+template <typename T, bool MULTI> struct MultiArg {
+  __device__ const MultiPhase<T>* get() const { return nullptr; }
+};
+template <typename T> struct MultiArg<T, true> {
+  MultiPhase<T> m;
+  __device__ const MultiPhase<T>* get() const { return &m; }
+};
+
 // a * b exactly as hi + lo (b float-float): hi = a b.hi rounded, lo = the rest
 __device__ __forceinline__ float prod_hi_lo(float a, ff b, float& lo) {
   const float hi = a * b.hi;
@@ -703,9 +758,21 @@ template <bool SMEM, typename C> __device__ __forceinline__ C ld_node(const C* p
 // only when the window is the whole half spectrum; for a pruned window no
 // point can reach its edge, and the index clamps below only keep every read
 // in bounds for non-finite input (whose result is NaN through the phase).
-template <bool SMEM, bool EDGE>
+// phase of one offset (PX, PY float-float) in turns, reduced exactly to
+// |f| <= 1/2: each product hi is reduced by its own nearest integer before the
+// sum, then the low parts are added
+__device__ __forceinline__ float phase_turns(float u, float v, ff PX, ff PY) {
+  float pae, pbe;
+  const float pa = prod_hi_lo(u, PX, pae), pb = prod_hi_lo(v, PY, pbe);
+  float f = (pa - rintf(pa)) + (pb - rintf(pb));
+  f += pae + pbe;
+  return f - rintf(f);
+}
+
+template <bool SMEM, bool EDGE, bool MULTI = false>
 __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__ Gp, const Window& w,
-                                               const GatherT<float>& p, float u, float v) {
+                                               const GatherT<float>& p, float u, float v,
+                                               const MultiPhase<float>* mp = nullptr) {
   float xae, xbe, yae, ybe;
   const float xa = prod_hi_lo(u, p.A, xae), xb = prod_hi_lo(v, p.B, xbe);
   const float ya = prod_hi_lo(u, p.B, yae), yb = prod_hi_lo(v, p.A, ybe);
@@ -756,15 +823,24 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
   const float Vr = fmaf(fv, br - ar, ar);
   float Vi = fmaf(fv, bi - ai, ai);
   if (neg) Vi = -Vi;
-  // phase in turns, reduced exactly: each product hi is reduced by its own
-  // nearest integer before the sum, then the low parts are added
-  float pae, pbe;
-  const float pa = prod_hi_lo(u, p.PX, pae), pb = prod_hi_lo(v, p.PY, pbe);
-  float f = (pa - rintf(pa)) + (pb - rintf(pb));
-  f += pae + pbe;
-  f -= rintf(f);
   float sn, cs;
-  __sincosf(6.28318530717958647692f * f, &sn, &cs);  // |arg| <= pi
+  if constexpr (MULTI) {
+    cs = 0.f;
+    sn = 0.f;
+    for (int k = 0; k < mp->K; ++k) {
+      ff PX, PY;
+      PX.hi = mp->PXs[k];
+      PX.lo = mp->PXsl[k];
+      PY.hi = mp->PYs[k];
+      PY.lo = mp->PYsl[k];
+      float sk, ck;
+      __sincosf(6.28318530717958647692f * phase_turns(u, v, PX, PY), &sk, &ck);  // |arg| <= pi
+      cs = fmaf(mp->amps[k], ck, cs);
+      sn = fmaf(mp->amps[k], sk, sn);
+    }
+  } else {
+    __sincosf(6.28318530717958647692f * phase_turns(u, v, p.PX, p.PY), &sn, &cs);  // |arg| <= pi
+  }
   return make_float2(Vr * cs - Vi * sn, Vr * sn + Vi * cs);
 }
 
@@ -904,10 +980,24 @@ __device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, c
   A1 = lerp(node(tx.y, ty.y), fu.y, fv.y);
 }
 
-template <bool SMEM, bool EDGE>
+// phase of one offset for both lanes, in turns, reduced to |f| <= 1/2:
+// (u dRA, v dDec) per lane, each reduced by its nearest integer, then summed
+// with the low parts
+__device__ __forceinline__ float2 phase_turns2(float2 U, float2 Vv, float2 PXh, float2 PXl,
+                                               float2 PYh, float2 PYl, float2 m1) {
+  const float2 pa = mul2(U, PXh), pb = mul2(Vv, PYh);
+  const float2 pe1 = fma2(U, PXl, fma2(U, PXh, mul2(pa, m1)));
+  const float2 pe2 = fma2(Vv, PYl, fma2(Vv, PYh, mul2(pb, m1)));
+  const float2 ra = fma2(rint_fma2(pa), m1, pa);  // exact, |ra| <= 1
+  const float2 rb = fma2(rint_fma2(pb), m1, pb);
+  const float2 f = add2(add2(ra, rb), add2(pe1, pe2));
+  return fma2(rint_fma2(f), m1, f);
+}
+
+template <bool SMEM, bool EDGE, bool MULTI = false>
 __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const Window& w,
                                             const Pair2Const& k, float2 U, float2 Vv, float2& V0,
-                                            float2& V1) {
+                                            float2& V1, const MultiPhase<float>* mp = nullptr) {
   // x = u A - v B, y = u B + v A, both lanes at once, as hi + lo
   float2 e1, e2, e3, e4, ex, ey;
   const float2 p1 = prod2(U, k.Ah, k.nAh, k.Al, e1);    //  u A
@@ -918,20 +1008,31 @@ __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const 
   const float2 p4 = prod2(Vv, k.Ah, k.nAh, k.Al, e4);   //  v A
   const float2 yh2 = two_sum2(p3, p4, k.m1, ey);
   const float2 yl2 = add2(ey, add2(e3, e4));
-  // phase in turns: (u dRA, v dDec) per lane, each reduced by its nearest
-  // integer, then summed with the low parts
-  float2 pe1, pe2;
-  const float2 pa = mul2(U, k.PXh), pb = mul2(Vv, k.PYh);
-  pe1 = fma2(U, k.PXl, fma2(U, k.PXh, mul2(pa, k.m1)));
-  pe2 = fma2(Vv, k.PYl, fma2(Vv, k.PYh, mul2(pb, k.m1)));
-  const float2 ra = fma2(rint_fma2(pa), k.m1, pa);  // exact, |ra| <= 1
-  const float2 rb = fma2(rint_fma2(pb), k.m1, pb);
-  float2 f = add2(add2(ra, rb), add2(pe1, pe2));
-  f = fma2(rint_fma2(f), k.m1, f);  // |f| <= 1/2
-  const float2 ang = mul2(f, k.twopi);  // |angle| <= pi
+  // phase factor c + i s per lane: one offset, or the amplitude-weighted sum
+  // over the copies of a multi-source model
   float s0, c0, s1, c1;
-  __sincosf(ang.x, &s0, &c0);
-  __sincosf(ang.y, &s1, &c1);
+  if constexpr (MULTI) {
+    float2 C = pk(0.f, 0.f), S = pk(0.f, 0.f);
+    for (int j = 0; j < mp->K; ++j) {
+      const float2 ang = mul2(phase_turns2(U, Vv, mp->PXh[j], mp->PXl[j], mp->PYh[j],
+                                           mp->PYl[j], k.m1),
+                              k.twopi);  // |angle| <= pi
+      float sa, ca, sb, cb;
+      __sincosf(ang.x, &sa, &ca);
+      __sincosf(ang.y, &sb, &cb);
+      C = fma2(mp->amp[j], pk(ca, cb), C);
+      S = fma2(mp->amp[j], pk(sa, sb), S);
+    }
+    c0 = C.x;
+    c1 = C.y;
+    s0 = S.x;
+    s1 = S.y;
+  } else {
+    const float2 ang = mul2(phase_turns2(U, Vv, k.PXh, k.PXl, k.PYh, k.PYl, k.m1),
+                            k.twopi);  // |angle| <= pi
+    __sincosf(ang.x, &s0, &c0);
+    __sincosf(ang.y, &s1, &c1);
+  }
   // Hermitian fold per lane
   const bool n0 = xh2.x < 0.f, n1 = xh2.y < 0.f;
   const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
@@ -967,9 +1068,10 @@ __device__ __forceinline__ void cell_d(double x, int ofs, int last, int& c, doub
   }
 }
 
-template <bool SMEM, bool EDGE>
+template <bool SMEM, bool EDGE, bool MULTI = false>
 __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict__ Gp, const Window& w,
-                                                const GatherT<double>& p, double u, double v) {
+                                                const GatherT<double>& p, double u, double v,
+                                                const MultiPhase<double>* mp = nullptr) {
   if (!(isfinite(u) && isfinite(v)))
     return make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
   double up = u * p.cpa - v * p.spa;
@@ -988,10 +1090,22 @@ __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict
   const double2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
   double2 V = clerp(clerp(g00, g01, fc), clerp(g10, g11, fc), fr);
   if (neg) V.y = -V.y;
-  const double ph = u * p.phx + v * p.phy;
-  const double fph = ph - rint(ph);
   double sn, cs;
-  sincospi(2.0 * fph, &sn, &cs);
+  if constexpr (MULTI) {
+    cs = 0.0;
+    sn = 0.0;
+    for (int k = 0; k < mp->K; ++k) {
+      const double ph = u * mp->phx[k] + v * mp->phy[k];
+      double sk, ck;
+      sincospi(2.0 * (ph - rint(ph)), &sk, &ck);
+      cs = fma(mp->amp[k], ck, cs);
+      sn = fma(mp->amp[k], sk, sn);
+    }
+  } else {
+    const double ph = u * p.phx + v * p.phy;
+    const double fph = ph - rint(ph);
+    sincospi(2.0 * fph, &sn, &cs);
+  }
   return cmul(V, make_double2(cs, sn));
 }
 
@@ -1087,16 +1201,16 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
 
 // Loop over this thread's uv points, reading the window nodes through G
 // (SMEM: G points into shared memory).
-template <typename T, bool CHI2, bool SMEM, bool EDGE, typename ACC>
+template <typename T, bool CHI2, bool SMEM, bool EDGE, bool MULTI, typename ACC>
 __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
                                               const GatherT<T>& p, const T* __restrict__ u,
                                               const T* __restrict__ v, const T* __restrict__ re,
                                               const T* __restrict__ im, const T* __restrict__ w,
                                               int64_t M, int vec, cplx_t<T>* __restrict__ vis,
-                                              ACC& acc) {
+                                              ACC& acc, const MultiPhase<T>* mp) {
   using C = cplx_t<T>;
   constexpr int W = Vec16<T>::W;
-  auto point = [&](T uu, T vv) { return sample_point<SMEM, EDGE>(G, win, p, uu, vv); };
+  auto point = [&](T uu, T vv) { return sample_point<SMEM, EDGE, MULTI>(G, win, p, uu, vv, mp); };
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
@@ -1118,8 +1232,8 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
       for (int e = 0; e < W; e += 2)
-        sample_pair<SMEM, EDGE>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]), Vs[e],
-                                Vs[e + 1]);
+        sample_pair<SMEM, EDGE, MULTI>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]),
+                                       Vs[e], Vs[e + 1], mp);
     } else {
 #pragma unroll
       for (int e = 0; e < W; ++e) Vs[e] = point(uu[e], vv[e]);
@@ -1155,10 +1269,12 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 // shared memory (32 warps share one copy), 256-thread blocks otherwise
 template <bool SMEM> constexpr int gather_threads() { return SMEM ? 1024 : 256; }
 
-template <typename T, bool CHI2, bool SMEM, bool EDGE, int K>
+template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false>
 __global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 1 : 3)
-gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes) {
+gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes,
+              const __grid_constant__ MultiArg<T, MULTI> multi) {
   using C = cplx_t<T>;
+  const MultiPhase<T>* mp = multi.get();
   const GatherJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   const C* __restrict__ Gw = jb.Gw;
   const GatherT<T>& p = jb.p;
@@ -1214,7 +1330,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
         for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
         __syncthreads();
       }
-      gather_points<T, CHI2, true, EDGE>(sw, win, p, u, v, re, im, w, M, vec, vis, acc);
+      gather_points<T, CHI2, true, EDGE, MULTI>(sw, win, p, u, v, re, im, w, M, vec, vis, acc, mp);
     } else {
       // the host sizes the shared window from the same extent, so this is
       // never taken; the result is NaN rather than a read out of bounds
@@ -1228,7 +1344,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
       }
     }
   } else {
-    gather_points<T, CHI2, false, EDGE>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc);
+    gather_points<T, CHI2, false, EDGE, MULTI>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc, mp);
   }
   if constexpr (CHI2) {
     __shared__ double ws[32];
@@ -1259,6 +1375,21 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
+// the current device (the attribute is per device; set once per size).
+template <auto Kern> cudaError_t ensure_smem_attr(size_t smem) {
+  constexpr int kDev = 64;
+  static size_t done[kDev] = {};
+  if (smem <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  if (dev >= 0 && dev < kDev && done[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kDev) done[dev] = smem;
+  return e;
+}
 
 // Launch `kern` as a programmatic dependent of the preceding kernel in `st`:
 // it may be scheduled while that kernel finishes, and waits for it in
@@ -1451,7 +1582,7 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
                               const T* u, const T* v, const T* re, const T* im, const T* w,
                               int64_t M, void* vis, double* partials, unsigned* counter,
                               double* chi2, size_t window_smem, bool edge, int blocks,
-                              cudaStream_t st) {
+                              const MultiSources* ms, cudaStream_t st) {
   using C = cplx_t<T>;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   int vec = al16(u) && al16(v);
@@ -1470,22 +1601,31 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
   jb.j[0] = GatherJob<T>{g, p, rho2, u, v, re, im, w, M, vec, static_cast<C*>(vis), partials,
                          counter, chi2};
   cudaError_t le = cudaSuccess;
-  auto go = [&](auto kern, size_t smem) {
-    le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes);
+  auto pick = [&](auto chi2_c, auto smem_c, auto edge_c) {
+    constexpr bool CH = decltype(chi2_c)::value, SM = decltype(smem_c)::value,
+                   ED = decltype(edge_c)::value;
+    const size_t smem = SM ? window_smem : 0;
+    if (ms && ms->K > 0) {
+      constexpr auto kern = gather_kernel<T, CH, SM, ED, 1, true>;
+      le = ensure_smem_attr<kern>(smem);
+      MultiArg<T, true> ma;
+      ma.m = MultiPhase<T>::make(ms->K, ms->dRA, ms->dDec, ms->amp);
+      if (le == cudaSuccess)
+        le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes, ma);
+    } else {
+      constexpr auto kern = gather_kernel<T, CH, SM, ED, 1, false>;
+      le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes,
+                            MultiArg<T, false>{});
+    }
   };
+  using TT = std::true_type;
+  using FF = std::false_type;
   if (chi2) {
-    if (window_smem)
-      edge ? go(gather_kernel<T, true, true, true, 1>, window_smem)
-           : go(gather_kernel<T, true, true, false, 1>, window_smem);
-    else
-      edge ? go(gather_kernel<T, true, false, true, 1>, 0) : go(gather_kernel<T, true, false, false, 1>, 0);
+    if (window_smem) edge ? pick(TT{}, TT{}, TT{}) : pick(TT{}, TT{}, FF{});
+    else edge ? pick(TT{}, FF{}, TT{}) : pick(TT{}, FF{}, FF{});
   } else {
-    if (window_smem)
-      edge ? go(gather_kernel<T, false, true, true, 1>, window_smem)
-           : go(gather_kernel<T, false, true, false, 1>, window_smem);
-    else
-      edge ? go(gather_kernel<T, false, false, true, 1>, 0)
-           : go(gather_kernel<T, false, false, false, 1>, 0);
+    if (window_smem) edge ? pick(FF{}, TT{}, TT{}) : pick(FF{}, TT{}, FF{});
+    else edge ? pick(FF{}, FF{}, TT{}) : pick(FF{}, FF{}, FF{});
   }
   if (le != cudaSuccess) return le;
   return cudaGetLastError();

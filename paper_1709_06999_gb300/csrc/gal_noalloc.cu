@@ -123,7 +123,7 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
   gp.phy = dDec;
   gp.N = nxy;
   if (gal::Launch<float>::gather(Gw, gp, rho2, u, v, re, im, w, M, nullptr, partials, counter,
-                                 chi2_out, 0, true, s->gather_blocks, cs) != cudaSuccess)
+                                 chi2_out, 0, true, s->gather_blocks, nullptr, cs) != cudaSuccess)
     return GAL_E_CUDA;
   return GAL_OK;
 }

@@ -133,6 +133,26 @@ def check_shift_equals_phase(O):
         assert np.max(np.abs(a - b)) < 1e-12, (i, j)
 
 
+def check_multi_source_equals_composite_image(O):
+    """K copies placed in the image by whole pixels, with amplitudes, have at
+    the grid nodes exactly the visibilities of the centred model times the
+    amplitude-weighted sum of the copies' phase factors (Sect. 3.1, 3.2)."""
+    n, dxy = 32, 0.05 * ARCSEC
+    x, y = pixel_xy(n, dxy)
+    u, v = node_uv(n, dxy)
+    base = np.zeros((n, n))
+    base[n // 2, n // 2] = 1.0
+    base[n // 2 + 1, n // 2 - 2] = 0.5            # an extended, asymmetric model
+    spots = [(10, 20, 1.0), (25, 4, -0.7), (3, 30, 2.5)]
+    composite = np.zeros((n, n))
+    for i, j, a in spots:
+        composite += a * np.roll(base, (i - n // 2, j - n // 2), axis=(0, 1))
+    want = O.sample_image(composite, dxy, u, v)
+    got = O.sample_image_multi(base, dxy, u, v, [x[j] for _, j, _ in spots],
+                               [y[i] for i, _, _ in spots], [a for _, _, a in spots])
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
 def check_zero_spacing_total_flux(O, seed=14):
     """V(0, 0) is the sum of the image (Jy/pixel summed is Jy)."""
     rng = np.random.default_rng(seed)
@@ -422,4 +442,5 @@ ALL_CHECKS = [
     check_sweep_pixels,
     check_image_size_table,
     check_uv_from_frequency,
+    check_multi_source_equals_composite_image,
 ]

@@ -46,6 +46,10 @@ MUTANTS = {
     "size_round_down": ("nxy = 2 ** (expo - 1) if mant == 0.5 else 2 ** expo", "nxy = 2 ** (expo - 1)"),
     "freq_wavelength_inverted": ("return (u_m * nu) / SPEED_OF_LIGHT, (v_m * nu) / SPEED_OF_LIGHT",
                                  "return (u_m / nu) * SPEED_OF_LIGHT, (v_m / nu) * SPEED_OF_LIGHT"),
+    "multi_no_amplitude": ("        total = total + a * sample_image(image, dxy, u, v, x, y, PA)",
+                           "        total = total + sample_image(image, dxy, u, v, x, y, PA)"),
+    "multi_swapped_offsets": ("        total = total + a * sample_image(image, dxy, u, v, x, y, PA)",
+                              "        total = total + a * sample_image(image, dxy, u, v, y, x, PA)"),
     "size_pixel_from_extent": ("return int(nxy), 1.0 / (nxy * duv)",
                                "return int(nxy), 1.0 / (2.0 * f_max * rho_max)"),
 }
