@@ -1214,11 +1214,13 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
-  // whole grid-stride rounds, then the remaining groups spread over all
-  // blocks (thread t of block b takes group t * gridDim + b), so that no few
-  // blocks run one round more than the rest
+  // whole grid-stride rounds, then the R remaining groups in equal contiguous
+  // slices, one per block (coalesced, and no few blocks run a round more
+  // than the rest)
   const int64_t rounds = nq / gstride;
-  const int64_t rem_j = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+  const int64_t rem = nq - rounds * gstride;
+  const int64_t slice = (rem + gridDim.x - 1) / gridDim.x;  // <= blockDim.x
+  const int64_t rem_q = rounds * gstride + (int64_t)blockIdx.x * slice + threadIdx.x;
   auto group = [&](int64_t q) {  // the W points of group q
     T uu[W], vv[W], rr[W], ii[W], ww[W];
     load16(u, q, uu);
@@ -1253,7 +1255,7 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   };
   int64_t q = gtid;
   for (int64_t r = 0; r < rounds; ++r, q += gstride) group(q);
-  if (rem_j < nq - rounds * gstride) group(rounds * gstride + rem_j);
+  if (threadIdx.x < slice && rem_q < nq) group(rem_q);
   for (int64_t k = nq * W + gtid; k < M; k += gstride) {
     const C V = point(u[k], v[k]);
     if constexpr (CHI2) {
