@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
 # kernels launched for this workload (template arguments as ncu prints them)
 KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1>", 2: "col_fft3_kernel<float, 12, 1>",
-           3: "gather_kernel<float, 1, 1, 0, 1>"}
+           3: "gather_kernel<float, 1, 1, 0, 1, 0>"}
 
 
 def algorithmic_bytes(stage: int, nxy: int, M: int, Kc: int, nrw: int) -> float:
