@@ -26,8 +26,6 @@ constexpr int kStages = 4;    // 0 extent, 1 row pass, 2 column pass, 3 gather
 // blocks per SM for float, one for double
 constexpr size_t kWindowSmemF32 = 100 * 1024;
 constexpr size_t kWindowSmemF64 = 200 * 1024;
-// bytes of observation data prefetched into L2 (of 129 MB) during the column pass
-constexpr size_t kL2PrefetchBudget = 0;  // L2 prefetch during the column pass: off
 
 struct TimedStage {
   int stage;
@@ -224,26 +222,10 @@ gal::GatherParams gather_params(int nxy, double dxy, double dRA, double dDec, do
   return g;
 }
 
-// Ranges of the arrays the gather is about to stream, to be prefetched into L2
-// during the column pass: the front of each array, 80 MB in total at most.
-gal::L2Prefetch make_prefetch(std::initializer_list<const void*> ptrs, size_t bytes_each) {
-  gal::L2Prefetch pf{};
-  if (kL2PrefetchBudget == 0) return pf;
-  const size_t per = std::min<size_t>(bytes_each, kL2PrefetchBudget / ptrs.size()) & ~size_t(15);
-  for (const void* p : ptrs) {
-    if (!p || !aligned(p, 16) || per == 0) continue;
-    pf.ptr[pf.n] = p;
-    pf.bytes[pf.n] = per;
-    ++pf.n;
-  }
-  return pf;
-}
-
 // FFT of the image (or of the swept profile) into the pruned window ctx->Gw.
 template <typename T>
 int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
-             double dxy, const double* rho2, int kc_hint, const gal::L2Prefetch* pf,
-             cudaStream_t st) {
+             double dxy, const double* rho2, int kc_hint, cudaStream_t st) {
   GAL_TRY(ensure<T>(ctx, nxy));
   const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
   const double S = (double)nxy * dxy;
@@ -251,7 +233,7 @@ int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& s
     return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, st);
   }));
   GAL_TRY(stage(ctx, 2, st, [&] {
-    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, pf, st);
+    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, st);
   }));
   return GAL_OK;
 }
@@ -271,8 +253,7 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   GAL_TRY(stage(ctx, 0, st, [&] {
     return gal::Launch<T>::extent(u, v, M, ctx->rho2, ctx->aux_blocks, st);
   }));
-  const gal::L2Prefetch pf = make_prefetch({u, v}, (size_t)M * sizeof(T));
-  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, ctx->rho2, 0, &pf, st));
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, ctx->rho2, 0, st));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
   const int blocks = ctx->gather_blocks[prec_index<T>()][0];
   return stage(ctx, 3, st, [&] {
@@ -318,9 +299,7 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
   }
   using C = gal::cplx_t<T>;
   const gal::Bounds bd = gal::make_bounds(d->rho2_host, (double)nxy * dxy, nxy);
-  const gal::L2Prefetch pf =
-      make_prefetch({d->u, d->v, d->re, d->im, d->w}, (size_t)d->M * sizeof(T));
-  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, bd.Kc, &pf, st));
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, bd.Kc, st));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
   size_t wbytes;
   const int blocks = chi2_gather_shape<T>(ctx, bd, &wbytes);

@@ -86,7 +86,7 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
   int x = (kc + SH::G - 1) / SH::G;
   const int cap = 2 * current_device_sms();
   if (x > cap) x = cap;
-  kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, static_cast<const C*>(tw), x, L2Prefetch{});
+  kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, static_cast<const C*>(tw));
   return cudaGetLastError();
 }
 

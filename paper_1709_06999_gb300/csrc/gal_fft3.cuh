@@ -18,7 +18,7 @@
 // the padded addresses reduce to a per-thread base plus immediate offsets.
 //
 // The last stage is run by the caller: last_full() computes it completely,
-// pruned_pair() evaluates only X[j] and X[L-j] from its input.
+// pruned_pair3() evaluates only X[j] and X[L-j] from its input.
 #pragma once
 
 #include "gal_common.cuh"

@@ -4,5 +4,5 @@ namespace gal {
 template cudaError_t row_fft3<float>(const float*, const float*, const SweepParams&, int,
                                      const void*, void*, const double*, double, int*, cudaStream_t);
 template cudaError_t col_fft3<float>(const void*, void*, int, const void*, const double*, double,
-                                   int, const L2Prefetch*, cudaStream_t);
+                                   int, cudaStream_t);
 }  // namespace gal

@@ -5,5 +5,5 @@ template cudaError_t row_fft3<double>(const double*, const double*, const SweepP
                                       const void*, void*, const double*, double, int*,
                                       cudaStream_t);
 template cudaError_t col_fft3<double>(const void*, void*, int, const void*, const double*, double,
-                                   int, const L2Prefetch*, cudaStream_t);
+                                   int, cudaStream_t);
 }  // namespace gal

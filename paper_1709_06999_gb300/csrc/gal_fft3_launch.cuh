@@ -40,7 +40,7 @@ cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const
 
 template <typename T, int LG>
 cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
-                        int kc_hint, const L2Prefetch* pf, cudaStream_t st) {
+                        int kc_hint, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
@@ -53,13 +53,10 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
   int col_blocks = (kc + SH::G - 1) / SH::G;
   const int cap = 2 * current_device_sms();
   if (col_blocks > cap) col_blocks = cap;
-  L2Prefetch none{};
-  const L2Prefetch& p = pf ? *pf : none;
-  const int pf_blocks = p.n > 0 ? 16 : 0;
   Jobs<ColJob<T>, 1> jb;
   jb.j[0] = ColJob<T>{static_cast<const C*>(F1), static_cast<C*>(Gw), rho2, S};
-  return launch_dependent(kern, dim3(col_blocks + pf_blocks), dim3(SH::threads), smem, st, jb,
-                          static_cast<const C*>(tw), col_blocks, p);
+  return launch_dependent(kern, dim3(col_blocks), dim3(SH::threads), smem, st, jb,
+                          static_cast<const C*>(tw));
 }
 
 template <typename T, int LG>
@@ -83,12 +80,12 @@ template <typename T> constexpr int col3_max_lg() { return sizeof(T) == 4 ? 13 :
 
 template <typename T, int LG>
 cudaError_t col3_switch(int lg, const void* F1, void* Gw, const void* tw, const double* rho2,
-                        double S, int kc_hint, const L2Prefetch* pf, cudaStream_t st) {
+                        double S, int kc_hint, cudaStream_t st) {
   if constexpr (LG > col3_max_lg<T>()) {
     return cudaErrorNotSupported;
   } else {
-    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, pf, st);
-    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, pf, st);
+    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, st);
+    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, st);
   }
 }
 
@@ -107,9 +104,9 @@ cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, c
 
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, const L2Prefetch* pf, cudaStream_t st) {
+                     int kc_hint, cudaStream_t st) {
   constexpr int LG0 = ilog2c(FftV<T>::V);
-  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, pf, st);
+  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, st);
 }
 
 }  // namespace gal

@@ -21,15 +21,6 @@ struct GatherParams {
   int N;
 };
 
-// Byte ranges brought into L2 by extra blocks of the column pass, which
-// leaves HBM nearly idle; the gather streams them next.  Pointers 16-byte
-// aligned, sizes multiples of 16.
-struct L2Prefetch {
-  const void* ptr[5];
-  unsigned long long bytes[5];
-  int n;
-};
-
 // K offset copies of one model (multi-source composition): host arrays of
 // K offsets (radians) and amplitudes, K in [1, 16].
 struct MultiSources {
@@ -63,11 +54,9 @@ template <typename T> struct Launch {
   static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                               const void* tw, void* F1, const double* rho2, double S, int* err,
                               cudaStream_t st);
-  // kc_hint: kept columns if the host knows them (0: unknown); pf: ranges to
-  // prefetch into L2 while the pass runs (may be null)
+  // kc_hint: kept columns if the host knows them (0: unknown)
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
-                              const double* rho2, double S, int kc_hint, const L2Prefetch* pf,
-                              cudaStream_t st);
+                              const double* rho2, double S, int kc_hint, cudaStream_t st);
   // ms: multi-source offsets (null: the single offset of gp)
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
@@ -132,6 +121,6 @@ cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, c
                      void* F1, const double* rho2, double S, int* err, cudaStream_t st);
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, const L2Prefetch* pf, cudaStream_t st);
+                     int kc_hint, cudaStream_t st);
 
 }  // namespace gal

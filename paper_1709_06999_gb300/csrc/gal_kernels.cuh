@@ -468,43 +468,15 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
 // of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
 // r0 + nrw - 1 are written to the window Gw (nrw x Kc).  When the window is
 // pruned, only the kept frequencies +-j are evaluated.
-// Blocks col_blocks and above only issue L2 bulk prefetches of pf (64 KiB per
-// instruction, interleaved over the ranges so each is fetched front first).
-__device__ __forceinline__ void l2_prefetch(const L2Prefetch& pf, int tid, int nthreads) {
-  constexpr unsigned long long CH = 64ull * 1024;
-  unsigned long long nch[5], maxc = 0;
-  for (int a = 0; a < pf.n; ++a) {
-    nch[a] = (pf.bytes[a] + CH - 1) / CH;
-    maxc = nch[a] > maxc ? nch[a] : maxc;
-  }
-  for (unsigned long long g = tid; g < maxc * pf.n; g += nthreads) {
-    const int a = (int)(g % pf.n);
-    const unsigned long long k = g / pf.n;
-    if (k >= nch[a]) continue;
-    const unsigned long long off = k * CH;
-    const unsigned long long len = pf.bytes[a] - off < CH ? pf.bytes[a] - off : CH;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
-                     static_cast<const char*>(pf.ptr[a]) + off),
-                 "r"((unsigned)len)
-                 : "memory");
-  }
-}
-
 template <typename T, int LG, int K>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads)
-col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
-                int col_blocks, L2Prefetch pf) {
+col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw) {
   const ColJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   const cplx_t<T>* __restrict__ F1 = jb.F1;
   cplx_t<T>* __restrict__ Gw = jb.Gw;
   const double* __restrict__ rho2 = jb.rho2;
   const double S = jb.S;
   grid_dep_launch();  // the gather may start its prologue on the SMs we leave idle
-  if ((int)blockIdx.x >= col_blocks) {
-    l2_prefetch(pf, (blockIdx.x - col_blocks) * blockDim.x + threadIdx.x,
-                (gridDim.x - col_blocks) * blockDim.x);
-    return;
-  }
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
@@ -525,7 +497,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   C* B = base + (size_t)(G + g) * RS;
   auto sync = [] { __syncthreads(); };
   grid_dep_wait();  // F1 is the row pass's output
-  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += col_blocks * G) {
+  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += gridDim.x * G) {
     const int c = c0 + g;
     const bool act = c < bd.Kc;
     C v[V];
@@ -1557,11 +1529,10 @@ cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& s
 
 template <typename T>
 cudaError_t Launch<T>::col_pass(const void* F1, void* Gw, int N, const void* tw,
-                                const double* rho2, double S, int kc_hint, const L2Prefetch* pf,
-                                cudaStream_t st) {
+                                const double* rho2, double S, int kc_hint, cudaStream_t st) {
   using C = cplx_t<T>;
   if (N >= FftV<T>::V) {
-    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, pf, st);
+    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, st);
     if (e != cudaErrorNotSupported) return e;
   }
   const int P = N / 2 + 1;
