@@ -22,10 +22,9 @@ namespace {
 
 constexpr int kMaxLog2 = 13;  // nxy <= 8192
 constexpr int kStages = 4;    // 0 extent, 1 row pass, 2 column pass, 3 gather
-// largest spectrum window staged in shared memory by the chi2 gather: two
-// blocks per SM for float, one for double
-constexpr size_t kWindowSmemF32 = 100 * 1024;
-constexpr size_t kWindowSmemF64 = 200 * 1024;
+// largest spectrum window staged in shared memory by the chi2 gather (one
+// 1024-thread block per SM holds it; larger windows are read through L2)
+constexpr size_t kWindowSmem = 200 * 1024;
 
 struct TimedStage {
   int stage;
@@ -270,7 +269,7 @@ template <typename T> int chi2_gather_shape(gal_ctx* ctx, const gal::Bounds& bd,
   // Stage the kept spectrum window in shared memory when it is small enough
   // (the pruned windows of long-baseline-free data usually are).
   size_t wbytes = ((size_t)bd.nrw * bd.Kc * sizeof(C) + 15) & ~size_t(15);  // bulk-copy size
-  if (wbytes > (sizeof(T) == 4 ? kWindowSmemF32 : kWindowSmemF64)) wbytes = 0;
+  if (wbytes > kWindowSmem) wbytes = 0;
   int blocks = ctx->gather_blocks[prec_index<T>()][1];
   if (wbytes) {
     if (wbytes != ctx->smem_blocks_key[prec_index<T>()]) {
