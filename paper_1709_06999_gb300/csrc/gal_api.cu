@@ -22,8 +22,9 @@ namespace {
 
 constexpr int kMaxLog2 = 13;  // nxy <= 8192
 constexpr int kStages = 4;    // 0 extent, 1 row pass, 2 column pass, 3 gather
-// largest spectrum window staged in shared memory by the chi2 gather (one
-// 1024-thread block per SM holds it; larger windows are read through L2)
+// largest spectrum window staged in shared memory by the chi2 gather (two
+// blocks per SM while two copies fit, one above; larger windows are read
+// through L2)
 constexpr size_t kWindowSmem = 200 * 1024;
 
 struct TimedStage {

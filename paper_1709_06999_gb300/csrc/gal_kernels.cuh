@@ -1239,12 +1239,13 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
   }
 }
 
-// block shape: one 1024-thread block per SM when the window is staged in
-// shared memory (32 warps share one copy), 256-thread blocks otherwise
-template <bool SMEM> constexpr int gather_threads() { return SMEM ? 1024 : 256; }
+// block shape: 512-thread blocks, two per SM, when the window is staged in
+// shared memory (each block its own copy, so one block's window copy and
+// final reduction overlap the other's stream), 256-thread blocks otherwise
+template <bool SMEM> constexpr int gather_threads() { return SMEM ? 512 : 256; }
 
 template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false>
-__global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 1 : 3)
+__global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 2 : 3)
 gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes,
               const __grid_constant__ MultiArg<T, MULTI> multi) {
   using C = cplx_t<T>;
