@@ -173,3 +173,25 @@ def test_invalid_request_launches_nothing():
     assert ctx.launch_count() == n0
     out = ctx.chi2_batch([])
     assert out.numel() == 0
+
+
+def test_cube_channels_at_their_sizes_match_oracle():
+    """Keplerian cube channels at the cube's image sides (512-2048) and
+    observation sizes (1e5-2e5 points) through one batch, against the oracle."""
+    ctx = Context(0)
+    dt = torch.float32
+    cube = synth.spectral_cube(n_chan=6, sizes=(512, 1024, 2048), m_lo=100_000, m_hi=200_000,
+                               seed=21)
+    reqs, keep = [], []
+    for ch in cube:
+        obs = make_obs(ctx, ch.u, ch.v, ch.w, ch.noise_re, ch.noise_im, dt)
+        img = dev(ch.image, dt)
+        keep.append((obs, img))
+        reqs.append(Request(obs, image=img, dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec, PA=ch.PA))
+    assert {r.nxy for r in reqs} == {512, 1024, 2048}
+    got = ctx.chi2_batch(reqs).cpu().numpy()
+    for r, g in zip(reqs, got):
+        u, v, re, im, w = (t.double().cpu().numpy() for t in r.obs._tensors)
+        ref = oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w, r.dRA,
+                                r.dDec, r.PA)
+        assert abs(g - ref) <= TOL_CHI2[dt] * abs(ref), (r.nxy, g, ref)

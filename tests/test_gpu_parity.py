@@ -308,13 +308,14 @@ def test_workspace_regrowth_and_counters(ctx):
 
 # ----------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration (registered observation,
-# chi2_image float32): chi2 over all 5e6 points and visibilities at sampled
-# points, against the oracle
+# chi2_image; float32 is the bench line, float64 its plain FP64 comparison):
+# chi2 over all 5e6 points and visibilities at sampled and all points, against
+# the oracle
 # ----------------------------------------------------------------------------
-def test_large_image_case_float32(ctx):
+@pytest.mark.parametrize("dt", DTYPES, ids=IDS)
+def test_large_image_case(ctx, dt):
     s = synth()
     p = s.large_image_problem()
-    dt = torch.float32
     R = lambda a: rounded(a, dt)  # noqa: E731
     G = O.half_spectrum(R(p.image))
     model = O.sample_spectrum(G, p.image.shape[0], p.dxy, R(p.u), R(p.v), p.dRA, p.dDec, p.PA)
