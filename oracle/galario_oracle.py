@@ -20,6 +20,12 @@ App. D).  Every other step is written out in the order of App. D:
     translate by (dRA, dDec)           Sect. 3.2 + App. D (phase factor)
     chi-square                         Sect. 3.1, Eq. (chap6.eq:def.chi.square)
 
+Two variants extend that path: the primary-beam factor A (Sect. 2.1, and
+assumption (ii) of the first release's list) multiplied into the image before
+the transform, and the complex-to-complex full-plane spectrum (whose agreement
+with the real-to-complex one the paper names as a consistency check, Sect. 5)
+sampled without the Hermitian fold; ``numpy.fft.fft2`` serves as its step.
+
 Readings of points the paper leaves open or states inconsistently are listed
 in the design notes; the ones that change arithmetic are repeated in the
 docstrings below.  Pins: every function here is checked, on the CPU, against
@@ -34,6 +40,9 @@ import numpy as np
 
 __all__ = [
     "pixel_coordinates",
+    "primary_beam",
+    "full_spectrum",
+    "sample_full_spectrum",
     "sweep",
     "half_spectrum",
     "rotate_uv",
@@ -136,6 +145,21 @@ def rotate_uv(u, v, PA: float):
     return u * c - v * s, u * s + v * c
 
 
+def rotate_offsets(dRA: float, dDec: float, PA: float):
+    """(dRA', dDec') = 2 pi R (dRA, dDec): the offsets rotated with the same
+    matrix as the uv points, in radians per wavelength (Sect. 3.2, App. D)."""
+    c, s = math.cos(PA), math.sin(PA)
+    dRA_rot = 2.0 * math.pi * (dRA * c - dDec * s)
+    dDec_rot = 2.0 * math.pi * (dRA * s + dDec * c)
+    return dRA_rot, dDec_rot
+
+
+def phase_factor(urot, vrot, dRA_rot, dDec_rot):
+    """exp(+i theta), theta = u' dRA' + v' dDec' (Sect. 3.2; the sign is App. D's)."""
+    theta = urot * dRA_rot + vrot * dDec_rot
+    return np.cos(theta) + 1j * np.sin(theta)
+
+
 def uv_to_index(urot, vrot, nxy: int, dxy: float):
     """Fractional grid indices (row iv, column iu) of rotated uv points, and the fold mask.
 
@@ -186,30 +210,104 @@ def sample_spectrum(G, nxy: int, dxy: float, u, v, dRA: float = 0.0, dDec: float
     sign, under which a source moved East by dRA acquires exp(+2 pi i u dRA).
     """
     urot, vrot = rotate_uv(u, v, PA)
-    c, s = math.cos(PA), math.sin(PA)
-    dRA_rot = 2.0 * math.pi * (dRA * c - dDec * s)
-    dDec_rot = 2.0 * math.pi * (dRA * s + dDec * c)
+    dRA_rot, dDec_rot = rotate_offsets(dRA, dDec, PA)
     iv, iu, neg = uv_to_index(urot, vrot, nxy, dxy)
     vis = bilinear(G, iv, iu)
     vis = np.where(neg, np.conj(vis), vis)
-    theta = urot * dRA_rot + vrot * dDec_rot
-    return vis * (np.cos(theta) + 1j * np.sin(theta))
+    return vis * phase_factor(urot, vrot, dRA_rot, dDec_rot)
 
 
-def sample_image(image, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0):
+FOUR_LN2 = 4.0 * math.log(2.0)
+
+
+def primary_beam(nxy: int, dxy: float, fwhm: float, dRA: float = 0.0, dDec: float = 0.0,
+                 PA: float = 0.0):
+    """Normalised primary-beam response A at the sky position of every model pixel.
+
+    Sect. 2.1: the visibility is the transform of A I, A being the antenna
+    pattern normalised to 1 at the pointing centre; its central lobe is close
+    to a Gaussian of full width at half maximum K lambda / D.  Reading: A(s) =
+    exp(-4 ln 2 |s|^2 / fwhm^2), circular, centred on the phase centre s = 0.
+
+    A model pixel is placed on the sky by the same geometry as its
+    visibilities (Sect. 3.2): with (u', v') = R (u, v) (rotate_uv) and the
+    phase exp(+2 pi i (u dRA + v dDec)), pixel p = (x_j, y_i) contributes
+    exp(+2 pi i u . (R^T p + o)), o = (dRA, dDec), so it sits at
+        s_x =  x cos PA + y sin PA + dRA,   s_y = -x sin PA + y cos PA + dDec.
+    The beam stays on the pointing centre while the model moves.
+    """
+    if not (fwhm > 0.0):
+        raise ValueError("the beam width must be positive")
+    x, y = pixel_coordinates(nxy, dxy)
+    X = x[None, :]
+    Y = y[:, None]
+    c, s = math.cos(PA), math.sin(PA)
+    sx = X * c + Y * s + dRA
+    sy = -X * s + Y * c + dDec
+    return np.exp(-FOUR_LN2 * (sx * sx + sy * sy) / (fwhm * fwhm))
+
+
+def full_spectrum(image):
+    """Full-plane spectrum of a square image by the complex-to-complex 2D FFT.
+
+    The same transform as half_spectrum (shift, forward FFT e^{-2 pi i k n / N},
+    shift) but complex-to-complex and shifted back along both axes, so both
+    signs of u are kept: cell (r, c) is the visibility at u = (c - nxy/2) du,
+    v = (r - nxy/2) du.  The paper checks this transform against the
+    real-to-complex one (Sect. 5, consistency checks).
+    """
+    img = np.asarray(image, dtype=np.complex128)
+    n0, n1 = img.shape
+    if n0 != n1 or n0 % 2:
+        raise ValueError("image must be square with an even side")
+    return np.fft.fftshift(np.fft.fft2(np.fft.fftshift(img)))
+
+
+def sample_full_spectrum(Gf, nxy: int, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0,
+                         PA: float = 0.0):
+    """Visibilities at (u, v) from a full-plane spectrum: rotate, index, interpolate, translate.
+
+    As sample_spectrum, without the Hermitian fold: iu = nxy/2 + u'/du and
+    iv = nxy/2 + v'/du on the full node grid (rows and columns 0 .. nxy-1,
+    u and v from -nxy/2 to nxy/2 - 1 cells), clamped to it like App. D's
+    spline; no conjugation.
+    """
+    urot, vrot = rotate_uv(u, v, PA)
+    dRA_rot, dDec_rot = rotate_offsets(dRA, dDec, PA)
+    du = 1.0 / (nxy * dxy)
+    iu = nxy / 2.0 + urot / du
+    iv = nxy / 2.0 + vrot / du
+    vis = bilinear(Gf, iv, iu)
+    return vis * phase_factor(urot, vrot, dRA_rot, dDec_rot)
+
+
+def sample_image(image, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
+                 pb_fwhm: float = 0.0, full_plane: bool = False):
     """Synthetic visibilities (Jy) of a model image (Jy/pixel) at uv points (wavelengths).
 
     Sect. 2 (sampleImage) and Fig. 3: shift, FFT, shift, then sampling.
+    pb_fwhm > 0 multiplies the image by primary_beam() first (the image is
+    then the bare brightness I, not A I); full_plane selects the
+    complex-to-complex spectrum and the unfolded sampling.
     """
     img = np.asarray(image, dtype=np.float64)
-    return sample_spectrum(half_spectrum(img), img.shape[0], dxy, u, v, dRA, dDec, PA)
+    n = img.shape[0]
+    if pb_fwhm > 0.0:
+        img = img * primary_beam(n, dxy, pb_fwhm, dRA, dDec, PA)
+    if full_plane:
+        return sample_full_spectrum(full_spectrum(img), n, dxy, u, v, dRA, dDec, PA)
+    return sample_spectrum(half_spectrum(img), n, dxy, u, v, dRA, dDec, PA)
 
 
 def sample_profile(intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v,
-                   dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0):
-    """Synthetic visibilities of an axisymmetric profile: sweep, then sample_image (Sect. 2, Fig. 3)."""
+                   dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0,
+                   pb_fwhm: float = 0.0, full_plane: bool = False):
+    """Synthetic visibilities of an axisymmetric profile: sweep, then sample_image (Sect. 2, Fig. 3).
+
+    The beam, when given, is evaluated on the sky (pixel positions, not the
+    deprojected disc radius)."""
     img = sweep(intensity, Rmin, dR, nxy, dxy, inc)
-    return sample_image(img, dxy, u, v, dRA, dDec, PA)
+    return sample_image(img, dxy, u, v, dRA, dDec, PA, pb_fwhm, full_plane)
 
 
 def chi2(vis, re_obs, im_obs, w):
@@ -227,15 +325,18 @@ def chi2(vis, re_obs, im_obs, w):
 
 
 def chi2_image(image, dxy: float, u, v, re_obs, im_obs, w, dRA: float = 0.0, dDec: float = 0.0,
-               PA: float = 0.0):
+               PA: float = 0.0, pb_fwhm: float = 0.0, full_plane: bool = False):
     """chi2Image of Sect. 2: sample_image followed by the chi-square reduction."""
-    return chi2(sample_image(image, dxy, u, v, dRA, dDec, PA), re_obs, im_obs, w)
+    vis = sample_image(image, dxy, u, v, dRA, dDec, PA, pb_fwhm, full_plane)
+    return chi2(vis, re_obs, im_obs, w)
 
 
 def chi2_profile(intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v, re_obs, im_obs, w,
-                 dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0):
+                 dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0, inc: float = 0.0,
+                 pb_fwhm: float = 0.0, full_plane: bool = False):
     """chi2Profile of Sect. 2: sample_profile followed by the chi-square reduction."""
-    vis = sample_profile(intensity, Rmin, dR, nxy, dxy, u, v, dRA, dDec, PA, inc)
+    vis = sample_profile(intensity, Rmin, dR, nxy, dxy, u, v, dRA, dDec, PA, inc, pb_fwhm,
+                         full_plane)
     return chi2(vis, re_obs, im_obs, w)
 
 

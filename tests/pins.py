@@ -424,6 +424,136 @@ def check_uv_from_frequency(O):
     assert abs(u[1] - 5003.461) < 1e-3
 
 
+
+# ----------------------------------------------------------------------------
+# full-plane (complex-to-complex) spectrum and the primary beam
+# ----------------------------------------------------------------------------
+
+def check_full_spectrum_bruteforce(O, sizes=(4, 8, 16, 32), seed=31):
+    """Every node of the full-plane spectrum (both signs of u, no fold) equals
+    the direct DFT at u = (c - N/2) du, v = (r - N/2) du."""
+    rng = np.random.default_rng(seed)
+    for n in sizes:
+        dxy = 1.7e-7
+        img = rng.standard_normal((n, n))
+        G = O.full_spectrum(img)
+        du = 1.0 / (n * dxy)
+        r, c = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        ref = direct_dft(img, dxy, ((c - n // 2) * du).ravel(),
+                         ((r - n // 2) * du).ravel()).reshape(r.shape)
+        err = np.max(np.abs(G - ref)) / np.max(np.abs(ref))
+        assert err < 1e-13, (n, err)
+
+
+def check_full_plane_nodes_bruteforce(O, sizes=(8, 16, 32), seed=32):
+    """Full-plane sampling at the nodes of both half planes, including the
+    u = -N/2 column that only the full plane holds, equals the direct DFT."""
+    rng = np.random.default_rng(seed)
+    for n in sizes:
+        dxy = 2.3e-7
+        img = rng.standard_normal((n, n))
+        du = 1.0 / (n * dxy)
+        u, v = node_uv(n, dxy)
+        u = np.concatenate([u, np.full(n - 1, -(n // 2) * du)])
+        v = np.concatenate([v, (np.arange(n - 1) - (n // 2 - 1)) * du])
+        V = O.sample_image(img, dxy, u, v, full_plane=True)
+        assert normwise(V, direct_dft(img, dxy, u, v)) < 1e-13, n
+
+
+def check_full_plane_matches_half_plane(O, seed=33):
+    """Off the nodes, with rotation and offsets, the full-plane and the folded
+    half-plane samplings agree to rounding: bilinear interpolation commutes
+    with the mirror (u, v) -> (-u, -v) and the spectrum of a real image is
+    Hermitian (the paper's C2C versus R2C consistency check)."""
+    rng = np.random.default_rng(seed)
+    n, dxy = 64, 0.02 * ARCSEC
+    img = rng.standard_normal((n, n))
+    u, v = synth.uv_loguniform(400, 1e3, 0.4 / dxy, rng)
+    for PA, dRA, dDec in [(0.0, 0.0, 0.0), (1.1, 0.2 * ARCSEC, -0.35 * ARCSEC)]:
+        a = O.sample_image(img, dxy, u, v, dRA, dDec, PA)
+        b = O.sample_image(img, dxy, u, v, dRA, dDec, PA, full_plane=True)
+        assert normwise(b, a) < 1e-13, PA
+
+
+def rotate_to_nodes(ku, kv, du, PA):
+    """uv points whose rotated coordinates (Sect. 3.2 equations) are the
+    nodes (ku du, kv du): u = R^T k."""
+    c, s = math.cos(PA), math.sin(PA)
+    return (c * ku + s * kv) * du, (-s * ku + c * kv) * du
+
+
+def gaussian_beam_ft(u, v, A0, sigma, inc, fwhm, dRA, dDec, PA):
+    """Closed-form visibility of a model G(p) = A0 exp(-((x / cos inc)^2 + y^2)
+    / (2 sigma^2)) (model coordinates p = (x, y)) that is rotated by PA, moved
+    by o = (dRA, dDec) and seen through a circular Gaussian beam of FWHM fwhm
+    fixed on the pointing centre, A(s) = exp(-4 ln 2 |s|^2 / fwhm^2).
+
+    Derivation, with k = R u the rotated uv point and b = R o: the model point
+    p sits on the sky at R^T p + o, so
+        V(u) = e^{2 pi i u.o} int G(p) exp(-c |p + b|^2) e^{2 pi i k.p} dp,
+    c = 4 ln 2 / fwhm^2.  Per axis, with a the Gaussian's coefficient and
+    alpha = a + c, the integrand is exp(-alpha (x - x0)^2 - (a c / alpha) b^2)
+    with x0 = -(c / alpha) b, whose transform is
+        sqrt(pi / alpha) exp(-(a c / alpha) b^2) exp(-pi^2 k^2 / alpha)
+        e^{2 pi i k x0}."""
+    c4 = 4.0 * math.log(2.0) / fwhm ** 2
+    cp, sp = math.cos(PA), math.sin(PA)
+    ku = u * cp - v * sp
+    kv = u * sp + v * cp
+    bx = dRA * cp - dDec * sp
+    by = dRA * sp + dDec * cp
+    out = A0 * np.exp(2j * math.pi * (u * dRA + v * dDec))
+    for a, k, b in ((1.0 / (2.0 * (sigma * math.cos(inc)) ** 2), ku, bx),
+                    (1.0 / (2.0 * sigma ** 2), kv, by)):
+        alpha = a + c4
+        x0 = -(c4 / alpha) * b
+        out = out * math.sqrt(math.pi / alpha) * math.exp(-(a * c4 / alpha) * b * b) \
+            * np.exp(-(math.pi ** 2) * k * k / alpha) * np.exp(2j * math.pi * k * x0)
+    return out
+
+
+def check_beam_gaussian_closed_form(O):
+    """A circular Gaussian image through the primary beam, moved and rotated,
+    matches the closed-form transform at rotated nodes to 1e-10 (sigma = 12
+    px and an effective width >= 9 px: truncation and aliasing are far below
+    rounding).  Both the full-plane and the half-plane paths are checked."""
+    n, dxy = 256, 0.01 * ARCSEC
+    sigma, fwhm, A0 = 12 * dxy, 40 * dxy, 2.5e10
+    x, y = pixel_xy(n, dxy)
+    img = dxy * dxy * A0 * np.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / (2 * sigma ** 2))
+    du = 1.0 / (n * dxy)
+    K = np.arange(-40, 41, 3, dtype=np.float64)
+    ku, kv = (a.ravel() for a in np.meshgrid(K, K))
+    for PA, dRA, dDec in [(0.0, 0.0, 0.0), (0.0, 15 * dxy, -10 * dxy),
+                          (0.7, 15 * dxy, -10 * dxy), (2.2, -8 * dxy, 21 * dxy)]:
+        u, v = rotate_to_nodes(ku, kv, du, PA)
+        ref = gaussian_beam_ft(u, v, A0, sigma, 0.0, fwhm, dRA, dDec, PA)
+        for full in (False, True):
+            V = O.sample_image(img, dxy, u, v, dRA, dDec, PA, pb_fwhm=fwhm, full_plane=full)
+            assert normwise(V, ref) < 1e-10, (PA, dRA, full, normwise(V, ref))
+
+
+def check_beam_inclined_profile_closed_form(O):
+    """An inclined Gaussian profile through the beam (evaluated on the sky, not
+    on the deprojected disc) matches the closed form at rotated nodes; the
+    tolerance is set by the profile's linear interpolation (dR = sigma / 2000)."""
+    n, dxy = 256, 0.01 * ARCSEC
+    sigma, fwhm, A0 = 12 * dxy, 30 * dxy, 3.0e10
+    inc = 60 * synth.DEG
+    rmax = (n / 2) * math.sqrt(2) * dxy / math.cos(inc) * 1.01
+    dR = sigma / 2000
+    r = dR * np.arange(int(rmax / dR) + 2)
+    I = A0 * np.exp(-r ** 2 / (2 * sigma ** 2))
+    du = 1.0 / (n * dxy)
+    K = np.arange(-40, 41, 4, dtype=np.float64)
+    ku, kv = (a.ravel() for a in np.meshgrid(K, K))
+    for PA, dRA, dDec in [(0.0, 12 * dxy, 0.0), (1.3, -9 * dxy, 14 * dxy)]:
+        u, v = rotate_to_nodes(ku, kv, du, PA)
+        V = O.sample_profile(I, 0.0, dR, n, dxy, u, v, dRA, dDec, PA, inc, pb_fwhm=fwhm)
+        ref = gaussian_beam_ft(u, v, A0, sigma, inc, fwhm, dRA, dDec, PA)
+        assert normwise(V, ref) < 1e-6, (PA, normwise(V, ref))
+
+
 ALL_CHECKS = [
     check_half_spectrum_bruteforce,
     check_sample_nodes_bruteforce,
@@ -443,4 +573,9 @@ ALL_CHECKS = [
     check_image_size_table,
     check_uv_from_frequency,
     check_multi_source_equals_composite_image,
+    check_full_spectrum_bruteforce,
+    check_full_plane_nodes_bruteforce,
+    check_full_plane_matches_half_plane,
+    check_beam_gaussian_closed_form,
+    check_beam_inclined_profile_closed_form,
 ]

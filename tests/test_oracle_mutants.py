@@ -18,8 +18,8 @@ MUTANTS = {
     "no_output_shift": ("return np.fft.fftshift(np.fft.rfft2(centred), axes=0)",
                         "return np.fft.rfft2(centred)"),
     "transposed_image": ("centred = np.fft.fftshift(img)", "centred = np.fft.fftshift(img.T)"),
-    "phase_sign": ("return vis * (np.cos(theta) + 1j * np.sin(theta))",
-                   "return vis * (np.cos(theta) - 1j * np.sin(theta))"),
+    "phase_sign": ("return np.cos(theta) + 1j * np.sin(theta)",
+                   "return np.cos(theta) - 1j * np.sin(theta)"),
     "no_conjugate_fold": ("vis = np.where(neg, np.conj(vis), vis)", "vis = vis"),
     "no_v_flip_fold": ("iv = nxy / 2.0 + np.where(neg, -vrot, vrot) / du", "iv = nxy / 2.0 + vrot / du"),
     "rotation_direction": ("return u * c - v * s, u * s + v * c", "return u * c + v * s, -u * s + v * c"),
@@ -52,6 +52,19 @@ MUTANTS = {
                               "        total = total + a * sample_image(image, dxy, u, v, y, x, PA)"),
     "size_pixel_from_extent": ("return int(nxy), 1.0 / (nxy * duv)",
                                "return int(nxy), 1.0 / (2.0 * f_max * rho_max)"),
+    "full_plane_u_not_shifted": ("return np.fft.fftshift(np.fft.fft2(np.fft.fftshift(img)))",
+                                 "return np.fft.fftshift(np.fft.fft2(np.fft.fftshift(img)), axes=0)"),
+    "full_plane_no_input_shift": ("return np.fft.fftshift(np.fft.fft2(np.fft.fftshift(img)))",
+                                  "return np.fft.fftshift(np.fft.fft2(img))"),
+    "full_plane_u_mirrored": ("iu = nxy / 2.0 + urot / du", "iu = nxy / 2.0 - urot / du"),
+    "full_plane_conjugated": ("    vis = bilinear(Gf, iv, iu)\n", "    vis = np.conj(bilinear(Gf, iv, iu))\n"),
+    "beam_centre_sign": ("sx = X * c + Y * s + dRA", "sx = X * c + Y * s - dRA"),
+    "beam_rotation_direction": ("sx = X * c + Y * s + dRA\n    sy = -X * s + Y * c + dDec",
+                                "sx = X * c - Y * s + dRA\n    sy = X * s + Y * c + dDec"),
+    "beam_offsets_ignored": ("sy = -X * s + Y * c + dDec", "sy = -X * s + Y * c"),
+    "beam_no_4ln2": ("np.exp(-FOUR_LN2 * (sx * sx + sy * sy) / (fwhm * fwhm))",
+                     "np.exp(-(sx * sx + sy * sy) / (fwhm * fwhm))"),
+    "beam_transposed": ("X = x[None, :]\n    Y = y[:, None]", "X = x[:, None]\n    Y = y[None, :]"),
 }
 
 
