@@ -193,6 +193,62 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
                             double dRA, double dDec, double PA, const gal_data* data,
                             double* chi2_host, void* stream);
 
+/* ---- primary beam and full-plane spectrum ---------------------------------------------- */
+
+/* Options of the extended calls below; a NULL pointer means all defaults, and
+ * the call is then identical to its plain counterpart.
+ *
+ * pb_fwhm: full width at half maximum (radians) of a primary beam applied to
+ *   the model before the transform (Sect. 2.1: the visibility is the transform
+ *   of A I, A being the antenna pattern normalised at the pointing centre,
+ *   whose central lobe is close to a Gaussian of FWHM K lambda / D; the first
+ *   release left A to the caller and never applied it to profiles).  A is the
+ *   circular Gaussian exp(-4 ln 2 |s|^2 / pb_fwhm^2), fixed on the phase centre
+ *   and evaluated at each model pixel's sky position after the PA rotation and
+ *   the (dRA, dDec) move, so a model moved away from the centre is attenuated
+ *   as the sky would attenuate it.  The image (or the swept profile) is then
+ *   the bare brightness I.  0 = no beam; negative or non-finite values are
+ *   GAL_E_INVAL.  The factor is applied inside the row FFT (no extra pass).
+ * full_plane: 1 = compute the full complex-to-complex spectrum (both signs of
+ *   u, no Hermitian fold) instead of the real-to-complex half spectrum; the
+ *   paper checks one against the other (Sect. 5).  Off-grid points are
+ *   clamped to the node range -nxy/2 .. nxy/2-1 of both axes.  Supported for
+ *   16 <= nxy <= 8192 (_f32) and 8 <= nxy <= 4096 (_f64); other sizes, and
+ *   values other than 0 and 1, are GAL_E_INVAL. */
+typedef struct gal_opts {
+  double pb_fwhm;
+  int full_plane;
+} gal_opts;
+
+int gal_sample_image_ex_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                            double dDec, double PA, const gal_opts* opts, int64_t M,
+                            const float* u, const float* v, float* vis_out, void* stream);
+int gal_sample_image_ex_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                            double dDec, double PA, const gal_opts* opts, int64_t M,
+                            const double* u, const double* v, double* vis_out, void* stream);
+int gal_sample_profile_ex_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR,
+                              int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                              const gal_opts* opts, int64_t M, const float* u, const float* v,
+                              float* vis_out, void* stream);
+int gal_sample_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR,
+                              int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                              const gal_opts* opts, int64_t M, const double* u, const double* v,
+                              double* vis_out, void* stream);
+int gal_chi2_image_ex_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                          double dDec, double PA, const gal_opts* opts, const gal_data* data,
+                          double* chi2_out, void* stream);
+int gal_chi2_image_ex_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                          double dDec, double PA, const gal_opts* opts, const gal_data* data,
+                          double* chi2_out, void* stream);
+int gal_chi2_profile_ex_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                            double dxy, double inc, double dRA, double dDec, double PA,
+                            const gal_opts* opts, const gal_data* data, double* chi2_out,
+                            void* stream);
+int gal_chi2_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                            double dxy, double inc, double dRA, double dDec, double PA,
+                            const gal_opts* opts, const gal_data* data, double* chi2_out,
+                            void* stream);
+
 /* ---- multi-source composition --------------------------------------------------------- */
 
 /* Largest number of copies in one multi-source call. */

@@ -55,6 +55,22 @@ class GalRequest(ct.Structure):
                 ("data", P)]
 
 
+class GalOpts(ct.Structure):
+    """struct gal_opts of include/galario_gb300.h."""
+    _fields_ = [("pb_fwhm", D), ("full_plane", I32)]
+
+
+_OPTS = ct.POINTER(GalOpts)
+for _p in ("f32", "f64"):
+    _SIGNATURES.update({
+        f"gal_sample_image_ex_{_p}": (I32, [P, P, I32, D, D, D, D, _OPTS, I64, P, P, P, P]),
+        f"gal_sample_profile_ex_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, _OPTS, I64, P,
+                                              P, P, P]),
+        f"gal_chi2_image_ex_{_p}": (I32, [P, P, I32, D, D, D, D, _OPTS, P, P, P]),
+        f"gal_chi2_profile_ex_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, _OPTS, P, P, P]),
+    })
+
+
 class GalServerStats(ct.Structure):
     """struct gal_server_stats of include/galario_gb300.h."""
     _fields_ = [("submitted", ct.c_uint64), ("completed", ct.c_uint64),

@@ -34,6 +34,13 @@ def _check(ctx_handle, status: int):
         raise GalError(f"galario_gb300 status {status}: {msg}")
 
 
+def _opts(pb_fwhm: float, full_plane: bool):
+    """gal_opts for the extended calls, or None when both are at their defaults."""
+    if not pb_fwhm and not full_plane:
+        return None
+    return ct.byref(_native.GalOpts(float(pb_fwhm), 1 if full_plane else 0))
+
+
 def _suffix(*tensors) -> str:
     dt = tensors[0].dtype
     if dt not in _SUFFIX:
@@ -242,8 +249,10 @@ class Context:
         return out
 
     def sample_image(self, image, dxy: float, u, v, dRA: float = 0.0, dDec: float = 0.0,
-                     PA: float = 0.0, out=None):
-        """Visibilities as an (M, 2) tensor of (Re, Im)."""
+                     PA: float = 0.0, out=None, *, pb_fwhm: float = 0.0, full_plane: bool = False):
+        """Visibilities as an (M, 2) tensor of (Re, Im).  pb_fwhm > 0 applies a
+        primary beam of that FWHM (radians); full_plane uses the
+        complex-to-complex spectrum (gal_opts)."""
         img, u, v = self._dev(image), self._dev(u), self._dev(v)
         sfx = _suffix(img, u, v)
         nxy = img.shape[0]
@@ -252,47 +261,65 @@ class Context:
         m = u.numel()
         if out is None:
             out = torch.empty((m, 2), dtype=img.dtype, device=self.device)
-        fn = getattr(self.lib, f"gal_sample_image_{sfx}")
-        _check(self.handle, fn(self.handle, img.data_ptr(), nxy, dxy, dRA, dDec, PA, m,
-                               u.data_ptr(), v.data_ptr(), out.data_ptr(), self._stream()))
+        opts = _opts(pb_fwhm, full_plane)
+        head = (self.handle, img.data_ptr(), nxy, dxy, dRA, dDec, PA)
+        tail = (m, u.data_ptr(), v.data_ptr(), out.data_ptr(), self._stream())
+        if opts is None:
+            _check(self.handle, getattr(self.lib, f"gal_sample_image_{sfx}")(*head, *tail))
+        else:
+            _check(self.handle, getattr(self.lib, f"gal_sample_image_ex_{sfx}")(*head, opts, *tail))
         return out
 
     def sample_profile(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float, u, v,
                        inc: float = 0.0, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
-                       out=None):
+                       out=None, *, pb_fwhm: float = 0.0, full_plane: bool = False):
         I, u, v = self._dev(intensity), self._dev(u), self._dev(v)
         sfx = _suffix(I, u, v)
         m = u.numel()
         if out is None:
             out = torch.empty((m, 2), dtype=I.dtype, device=self.device)
-        fn = getattr(self.lib, f"gal_sample_profile_{sfx}")
-        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc,
-                               dRA, dDec, PA, m, u.data_ptr(), v.data_ptr(), out.data_ptr(),
-                               self._stream()))
+        opts = _opts(pb_fwhm, full_plane)
+        head = (self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc, dRA, dDec, PA)
+        tail = (m, u.data_ptr(), v.data_ptr(), out.data_ptr(), self._stream())
+        if opts is None:
+            _check(self.handle, getattr(self.lib, f"gal_sample_profile_{sfx}")(*head, *tail))
+        else:
+            _check(self.handle,
+                   getattr(self.lib, f"gal_sample_profile_ex_{sfx}")(*head, opts, *tail))
         return out
 
     def chi2_image(self, image, dxy: float, obs: Observation, dRA: float = 0.0, dDec: float = 0.0,
-                   PA: float = 0.0, out=None):
+                   PA: float = 0.0, out=None, *, pb_fwhm: float = 0.0, full_plane: bool = False):
         """chi2 as a one-element float64 device tensor (stream-ordered, no sync)."""
         img = self._dev(image)
         sfx = _suffix(img)
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=self.device)
-        fn = getattr(self.lib, f"gal_chi2_image_{sfx}")
-        _check(self.handle, fn(self.handle, img.data_ptr(), img.shape[0], dxy, dRA, dDec, PA,
-                               obs.handle, out.data_ptr(), self._stream()))
+        opts = _opts(pb_fwhm, full_plane)
+        head = (self.handle, img.data_ptr(), img.shape[0], dxy, dRA, dDec, PA)
+        tail = (obs.handle, out.data_ptr(), self._stream())
+        if opts is None:
+            _check(self.handle, getattr(self.lib, f"gal_chi2_image_{sfx}")(*head, *tail))
+        else:
+            _check(self.handle, getattr(self.lib, f"gal_chi2_image_ex_{sfx}")(*head, opts, *tail))
         return out
 
     def chi2_profile(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float,
                      obs: Observation, inc: float = 0.0, dRA: float = 0.0, dDec: float = 0.0,
-                     PA: float = 0.0, out=None):
+                     PA: float = 0.0, out=None, *, pb_fwhm: float = 0.0,
+                     full_plane: bool = False):
         I = self._dev(intensity)
         sfx = _suffix(I)
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=self.device)
-        fn = getattr(self.lib, f"gal_chi2_profile_{sfx}")
-        _check(self.handle, fn(self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc,
-                               dRA, dDec, PA, obs.handle, out.data_ptr(), self._stream()))
+        opts = _opts(pb_fwhm, full_plane)
+        head = (self.handle, I.data_ptr(), I.numel(), Rmin, dR, nxy, dxy, inc, dRA, dDec, PA)
+        tail = (obs.handle, out.data_ptr(), self._stream())
+        if opts is None:
+            _check(self.handle, getattr(self.lib, f"gal_chi2_profile_{sfx}")(*head, *tail))
+        else:
+            _check(self.handle,
+                   getattr(self.lib, f"gal_chi2_profile_ex_{sfx}")(*head, opts, *tail))
         return out
 
     def chi2_image_host(self, image_host, dxy: float, obs: Observation, dRA: float = 0.0,

@@ -50,6 +50,8 @@ struct gal_ctx {
   double* chi2_dev = nullptr;   // result slot for the host-buffer entry points
   void* stage_img = nullptr;    // image staging for the host-buffer entry points
   size_t stage_img_bytes = 0;
+  void* beam = nullptr;         // primary-beam tables of the last call with a beam
+  size_t beam_bytes = 0;
   void* tw[2][kMaxLog2 + 1] = {};
   int gather_blocks[2][2] = {};  // [f64?][chi2?], global-memory window
   size_t smem_blocks_key[2] = {};  // window bytes the cached count below is for
@@ -123,11 +125,12 @@ cudaError_t grow(void** p, size_t* have, size_t need) {
 
 template <typename T> constexpr int prec_index() { return sizeof(T) == 8 ? 1 : 0; }
 
-// Workspace and twiddles for images of side nxy in precision T.
-template <typename T> int ensure(gal_ctx* ctx, int nxy) {
+// Workspace and twiddles for images of side nxy in precision T (full: the
+// full-plane path, whose row pass keeps up to nxy columns).
+template <typename T> int ensure(gal_ctx* ctx, int nxy, bool full = false) {
   using C = gal::cplx_t<T>;
   const size_t spec = (size_t)nxy * (nxy / 2 + 1) * sizeof(C);
-  GAL_CUDA(ctx, grow(&ctx->F1, &ctx->F1_bytes, spec));
+  GAL_CUDA(ctx, grow(&ctx->F1, &ctx->F1_bytes, full ? (size_t)nxy * nxy * sizeof(C) : spec));
   GAL_CUDA(ctx, grow(&ctx->Gw, &ctx->Gw_bytes, 2 * spec));  // horizontal node pairs
   const int l = log2i(nxy);
   void*& tw = ctx->tw[prec_index<T>()][l];
@@ -222,18 +225,55 @@ gal::GatherParams gather_params(int nxy, double dxy, double dRA, double dDec, do
   return g;
 }
 
-// FFT of the image (or of the swept profile) into the pruned window ctx->Gw.
+// Options of the extended calls (gal_opts): primary-beam FWHM (0: none) and
+// the full-plane spectrum.
+struct CallOpts {
+  double pb_fwhm = 0.0;
+  bool full = false;
+};
+
+int read_opts(const gal_opts* o, CallOpts* out) {
+  CallOpts c;
+  if (o) {
+    if (!(o->pb_fwhm >= 0.0) || !std::isfinite(o->pb_fwhm)) return GAL_E_INVAL;
+    if (o->full_plane != 0 && o->full_plane != 1) return GAL_E_INVAL;
+    c.pb_fwhm = o->pb_fwhm;
+    c.full = o->full_plane == 1;
+  }
+  *out = c;
+  return GAL_OK;
+}
+
+// Primary-beam tables of a call into ctx->beam (*out = null without a beam).
+template <typename T>
+int beam_tables(gal_ctx* ctx, const CallOpts& o, int nxy, double dxy, double dRA, double dDec,
+                double PA, cudaStream_t st, const T** out) {
+  *out = nullptr;
+  if (!(o.pb_fwhm > 0.0)) return GAL_OK;
+  GAL_CUDA(ctx, grow(&ctx->beam, &ctx->beam_bytes, 2 * (size_t)nxy * sizeof(T)));
+  T* tab = static_cast<T*>(ctx->beam);
+  GAL_TRY(stage(ctx, 1, st, [&] {
+    return gal::Launch<T>::beam_table(tab, nxy, dxy, o.pb_fwhm, dRA, dDec, PA, st);
+  }));
+  *out = tab;
+  return GAL_OK;
+}
+
+// FFT of the image (or of the swept profile) into the pruned window ctx->Gw;
+// `beam` multiplies the pixels (null: none), `full` keeps both signs of u.
 template <typename T>
 int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
-             double dxy, const double* rho2, int kc_hint, cudaStream_t st) {
-  GAL_TRY(ensure<T>(ctx, nxy));
+             double dxy, const double* rho2, int kc_hint, cudaStream_t st,
+             const T* beam = nullptr, bool full = false) {
+  GAL_TRY(ensure<T>(ctx, nxy, full));
   const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
   const double S = (double)nxy * dxy;
   GAL_TRY(stage(ctx, 1, st, [&] {
-    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, st);
+    if (full) return gal::Plane<T>::rows(image, I, sp, nxy, tw, ctx->F1, rho2, S, beam, st);
+    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, beam, st);
   }));
   GAL_TRY(stage(ctx, 2, st, [&] {
-    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, st);
+    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, full, st);
   }));
   return GAL_OK;
 }
@@ -242,9 +282,10 @@ template <typename T>
 int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
                 double dxy, double dRA, double dDec, double PA, int64_t M, const T* u,
                 const T* v, T* vis, cudaStream_t st,
-                const gal::MultiSources* ms = nullptr) {
+                const gal::MultiSources* ms = nullptr, const CallOpts& o = CallOpts{}) {
   if (!ctx) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
+  if (o.full && (ms || !gal::Plane<T>::supported(nxy))) return GAL_E_INVAL;
   if (M < 0) return GAL_E_INVAL;
   if (M == 0) return GAL_OK;
   if (!u || !v || !vis) return GAL_E_INVAL;
@@ -253,8 +294,17 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   GAL_TRY(stage(ctx, 0, st, [&] {
     return gal::Launch<T>::extent(u, v, M, ctx->rho2, ctx->aux_blocks, st);
   }));
-  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, ctx->rho2, 0, st));
+  const T* beam;
+  GAL_TRY(beam_tables<T>(ctx, o, nxy, dxy, dRA, dDec, PA, st, &beam));
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, ctx->rho2, 0, st, beam, o.full));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
+  if (o.full) {
+    const int blocks = ctx->num_sms * gal::Plane<T>::gather_blocks_per_sm(false, 0);
+    return stage(ctx, 3, st, [&] {
+      return gal::Plane<T>::gather(ctx->Gw, gp, ctx->rho2, u, v, nullptr, nullptr, nullptr, M,
+                                   vis, nullptr, nullptr, nullptr, 0, true, blocks, st);
+    });
+  }
   const int blocks = ctx->gather_blocks[prec_index<T>()][0];
   return stage(ctx, 3, st, [&] {
     return gal::Launch<T>::gather(ctx->Gw, gp, ctx->rho2, u, v, nullptr, nullptr, nullptr, M,
@@ -288,10 +338,12 @@ template <typename T> int chi2_gather_shape(gal_ctx* ctx, const gal::Bounds& bd,
 template <typename T>
 int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& sp, int nxy,
               double dxy, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
-              cudaStream_t st, const gal::MultiSources* ms = nullptr) {
+              cudaStream_t st, const gal::MultiSources* ms = nullptr,
+              const CallOpts& o = CallOpts{}) {
   if (!ctx || !d || !chi2) return GAL_E_INVAL;
   if (d->device != ctx->device || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
+  if (o.full && (ms || !gal::Plane<T>::supported(nxy))) return GAL_E_INVAL;
   if (!aligned(chi2, sizeof(double))) return GAL_E_INVAL;
   if (d->M == 0) {
     GAL_CUDA(ctx, cudaMemsetAsync(chi2, 0, sizeof(double), st));
@@ -299,8 +351,25 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
   }
   using C = gal::cplx_t<T>;
   const gal::Bounds bd = gal::make_bounds(d->rho2_host, (double)nxy * dxy, nxy);
-  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, bd.Kc, st));
+  const T* beam;
+  GAL_TRY(beam_tables<T>(ctx, o, nxy, dxy, dRA, dDec, PA, st, &beam));
   const gal::GatherParams gp = gather_params(nxy, dxy, dRA, dDec, PA);
+  if (o.full) {
+    const int W = gal::full_cols(bd, nxy).W;
+    GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, W, st, beam, true));
+    size_t wbytes = ((size_t)bd.nrw * W * sizeof(C) + 15) & ~size_t(15);  // bulk-copy size
+    if (wbytes > kWindowSmem) wbytes = 0;
+    int blocks = ctx->num_sms * gal::Plane<T>::gather_blocks_per_sm(true, wbytes);
+    if (blocks > ctx->partials_len) blocks = ctx->partials_len;
+    return stage(ctx, 3, st, [&] {
+      return gal::Plane<T>::gather(ctx->Gw, gp, d->rho2, static_cast<const T*>(d->u),
+                                   static_cast<const T*>(d->v), static_cast<const T*>(d->re),
+                                   static_cast<const T*>(d->im), static_cast<const T*>(d->w),
+                                   d->M, nullptr, ctx->partials, ctx->counter, chi2, wbytes,
+                                   /*edge=*/bd.r0 == 0, blocks, st);
+    });
+  }
+  GAL_TRY(spectrum<T>(ctx, image, I, sp, nxy, dxy, d->rho2, bd.Kc, st, beam));
   size_t wbytes;
   const int blocks = chi2_gather_shape<T>(ctx, bd, &wbytes);
   return stage(ctx, 3, st, [&] {
@@ -314,42 +383,52 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
 
 template <typename T>
 int sample_image_t(gal_ctx* ctx, const T* image, int nxy, double dxy, double dRA, double dDec,
-                   double PA, int64_t M, const T* u, const T* v, T* vis, void* stream) {
+                   double PA, int64_t M, const T* u, const T* v, T* vis, void* stream,
+                   const gal_opts* opts = nullptr) {
+  CallOpts o;
+  GAL_TRY(read_opts(opts, &o));
   if (!image || !aligned(image, 2 * sizeof(T))) return GAL_E_INVAL;
   gal::SweepParams sp{};
   return sample_impl<T>(ctx, image, nullptr, sp, nxy, dxy, dRA, dDec, PA, M, u, v, vis,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), nullptr, o);
 }
 
 template <typename T>
 int sample_profile_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int nxy, double dxy,
                      double inc, double dRA, double dDec, double PA, int64_t M, const T* u,
-                     const T* v, T* vis, void* stream) {
+                     const T* v, T* vis, void* stream, const gal_opts* opts = nullptr) {
+  CallOpts o;
+  GAL_TRY(read_opts(opts, &o));
   GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
   if (!aligned(I, sizeof(T))) return GAL_E_INVAL;
   gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
   return sample_impl<T>(ctx, nullptr, I, sp, nxy, dxy, dRA, dDec, PA, M, u, v, vis,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), nullptr, o);
 }
 
 template <typename T>
 int chi2_image_t(gal_ctx* ctx, const T* image, int nxy, double dxy, double dRA, double dDec,
-                 double PA, const gal_data* d, double* chi2, void* stream) {
+                 double PA, const gal_data* d, double* chi2, void* stream,
+                 const gal_opts* opts = nullptr) {
+  CallOpts o;
+  GAL_TRY(read_opts(opts, &o));
   if (!image || !aligned(image, 2 * sizeof(T))) return GAL_E_INVAL;
   gal::SweepParams sp{};
   return chi2_impl<T>(ctx, image, nullptr, sp, nxy, dxy, dRA, dDec, PA, d, chi2,
-                      static_cast<cudaStream_t>(stream));
+                      static_cast<cudaStream_t>(stream), nullptr, o);
 }
 
 template <typename T>
 int chi2_profile_t(gal_ctx* ctx, const T* I, int nr, double Rmin, double dR, int nxy, double dxy,
                    double inc, double dRA, double dDec, double PA, const gal_data* d, double* chi2,
-                   void* stream) {
+                   void* stream, const gal_opts* opts = nullptr) {
+  CallOpts o;
+  GAL_TRY(read_opts(opts, &o));
   GAL_TRY(check_profile(I, nr, Rmin, dR, inc));
   if (!aligned(I, sizeof(T))) return GAL_E_INVAL;
   gal::SweepParams sp{Rmin, dR, dxy, inc, nr};
   return chi2_impl<T>(ctx, nullptr, I, sp, nxy, dxy, dRA, dDec, PA, d, chi2,
-                      static_cast<cudaStream_t>(stream));
+                      static_cast<cudaStream_t>(stream), nullptr, o);
 }
 
 // Multi-source arguments: K in [1, 16] finite offsets and amplitudes (host).
@@ -913,7 +992,7 @@ void gal_destroy(gal_ctx* ctx) {
   cudaDeviceSynchronize();
   for (void* p : {ctx->F1, ctx->Gw, (void*)ctx->partials, (void*)ctx->counter, (void*)ctx->rho2,
                   (void*)ctx->uvrange, ctx->batch_ws, (void*)ctx->batch_ctr,
-                  (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img})
+                  (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img, ctx->beam})
     if (p) cudaFree(p);
   for (auto& a : ctx->tw)
     for (void* p : a)
@@ -1200,6 +1279,57 @@ int gal_chi2_profile_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, dou
                          const gal_data* data, double* chi2_out, void* stream) {
   return chi2_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
                                 chi2_out, stream);
+}
+
+int gal_sample_image_ex_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                            double dDec, double PA, const gal_opts* opts, int64_t M,
+                            const float* u, const float* v, float* vis_out, void* stream) {
+  return sample_image_t<float>(ctx, image, nxy, dxy, dRA, dDec, PA, M, u, v, vis_out, stream,
+                               opts);
+}
+int gal_sample_image_ex_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                            double dDec, double PA, const gal_opts* opts, int64_t M,
+                            const double* u, const double* v, double* vis_out, void* stream) {
+  return sample_image_t<double>(ctx, image, nxy, dxy, dRA, dDec, PA, M, u, v, vis_out, stream,
+                                opts);
+}
+int gal_sample_profile_ex_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR,
+                              int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                              const gal_opts* opts, int64_t M, const float* u, const float* v,
+                              float* vis_out, void* stream) {
+  return sample_profile_t<float>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, M, u, v,
+                                 vis_out, stream, opts);
+}
+int gal_sample_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR,
+                              int nxy, double dxy, double inc, double dRA, double dDec, double PA,
+                              const gal_opts* opts, int64_t M, const double* u, const double* v,
+                              double* vis_out, void* stream) {
+  return sample_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, M, u, v,
+                                  vis_out, stream, opts);
+}
+int gal_chi2_image_ex_f32(gal_ctx* ctx, const float* image, int nxy, double dxy, double dRA,
+                          double dDec, double PA, const gal_opts* opts, const gal_data* data,
+                          double* chi2_out, void* stream) {
+  return chi2_image_t<float>(ctx, image, nxy, dxy, dRA, dDec, PA, data, chi2_out, stream, opts);
+}
+int gal_chi2_image_ex_f64(gal_ctx* ctx, const double* image, int nxy, double dxy, double dRA,
+                          double dDec, double PA, const gal_opts* opts, const gal_data* data,
+                          double* chi2_out, void* stream) {
+  return chi2_image_t<double>(ctx, image, nxy, dxy, dRA, dDec, PA, data, chi2_out, stream, opts);
+}
+int gal_chi2_profile_ex_f32(gal_ctx* ctx, const float* I, int nr, double Rmin, double dR, int nxy,
+                            double dxy, double inc, double dRA, double dDec, double PA,
+                            const gal_opts* opts, const gal_data* data, double* chi2_out,
+                            void* stream) {
+  return chi2_profile_t<float>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
+                               chi2_out, stream, opts);
+}
+int gal_chi2_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, double dR, int nxy,
+                            double dxy, double inc, double dRA, double dDec, double PA,
+                            const gal_opts* opts, const gal_data* data, double* chi2_out,
+                            void* stream) {
+  return chi2_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
+                                chi2_out, stream, opts);
 }
 
 int gal_chi2_image_host_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,

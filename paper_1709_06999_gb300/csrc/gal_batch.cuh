@@ -39,7 +39,7 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
     const BatchItem& b = it[idx[k]];
     jb.j[k] = RowJob<T>{static_cast<const T*>(b.image), static_cast<const T*>(b.I),
                         SWEEP ? sweep_cast<T>(b.sp) : SweepT<T>{}, static_cast<C*>(b.F1), b.rho2,
-                        b.S};
+                        b.S, /*beam=*/nullptr};
   }
   const C* twc = static_cast<const C*>(tw);
   if constexpr (!SWEEP) {
@@ -80,7 +80,8 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
   int kc = 1;
   for (int k = 0; k < n; ++k) {
     const BatchItem& b = it[idx[k]];
-    jb.j[k] = ColJob<T>{static_cast<const C*>(b.F1), static_cast<C*>(b.Gw), b.rho2, b.S};
+    jb.j[k] = ColJob<T>{static_cast<const C*>(b.F1), static_cast<C*>(b.Gw), b.rho2, b.S,
+                        /*full=*/0};
     kc = b.Kc > kc ? b.Kc : kc;
   }
   int x = (kc + SH::G - 1) / SH::G;

@@ -129,6 +129,22 @@ __host__ __device__ __forceinline__ Bounds make_bounds(double rho2, double S, in
   return b;
 }
 
+// Columns of the full-plane (complex-to-complex) window: u from -lo to hi
+// cells, stored as window columns 0 .. W-1 (column lo is u = 0).  A pruned
+// window keeps -(Kc-1) .. Kc-1 (every point stays two cells inside); the
+// whole plane keeps the node range -N/2 .. N/2-1 of the shifted spectrum.
+struct FullCols {
+  int lo, hi, W;
+};
+
+__host__ __device__ __forceinline__ FullCols full_cols(const Bounds& b, int N) {
+  FullCols f;
+  f.lo = b.Kc >= N / 2 + 1 ? N / 2 : b.Kc - 1;
+  f.hi = b.Kc - 1 < N / 2 - 1 ? b.Kc - 1 : N / 2 - 1;
+  f.W = f.lo + f.hi + 1;
+  return f;
+}
+
 // Bounds for the whole block: one thread evaluates them (FP64: GB300's FP64
 // pipe is narrow, so no per-thread FP64 work) and shares them.  Every thread
 // of the block must call it.

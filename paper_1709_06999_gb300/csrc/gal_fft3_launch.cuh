@@ -8,14 +8,15 @@ namespace gal {
 
 template <typename T, int LG, bool SWEEP>
 cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const void* tw,
-                        void* F1, const double* rho2, double S, int* err, cudaStream_t st) {
+                        void* F1, const double* rho2, double S, int* err, const T* beam,
+                        cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LG, N = 2 * M;
   using SH = Shape3<T, M, N>;
   const C* twc = static_cast<const C*>(tw);
   C* out = static_cast<C*>(F1);
   Jobs<RowJob<T>, 1> jb;
-  jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, out, rho2, S};
+  jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, out, rho2, S, beam};
   if constexpr (!SWEEP) {
     constexpr auto kern = row_fft3_kernel<T, LG, true, false, 1>;
     const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
@@ -40,7 +41,7 @@ cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const
 
 template <typename T, int LG>
 cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
-                        int kc_hint, cudaStream_t st) {
+                        int kc_hint, bool full, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
@@ -48,13 +49,13 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
-  const int P = N / 2 + 1;
+  const int P = full ? N : N / 2 + 1;  // most window columns
   const int kc = kc_hint > 0 && kc_hint <= P ? kc_hint : P;
   int col_blocks = (kc + SH::G - 1) / SH::G;
   const int cap = 2 * current_device_sms();
   if (col_blocks > cap) col_blocks = cap;
   Jobs<ColJob<T>, 1> jb;
-  jb.j[0] = ColJob<T>{static_cast<const C*>(F1), static_cast<C*>(Gw), rho2, S};
+  jb.j[0] = ColJob<T>{static_cast<const C*>(F1), static_cast<C*>(Gw), rho2, S, full ? 1 : 0};
   return launch_dependent(kern, dim3(col_blocks), dim3(SH::threads), smem, st, jb,
                           static_cast<const C*>(tw));
 }
@@ -62,15 +63,15 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
 template <typename T, int LG>
 cudaError_t row3_switch(int lg, const T* image, const T* I, const SweepParams& sp,
                         const void* tw, void* F1, const double* rho2, double S, int* err,
-                        cudaStream_t st) {
+                        const T* beam, cudaStream_t st) {
   if constexpr (LG > 12) {
     return cudaErrorNotSupported;
   } else {
     if (lg == LG) {
-      if (I) return launch_row3<T, LG, true>(image, I, sp, tw, F1, rho2, S, err, st);
-      return launch_row3<T, LG, false>(image, I, sp, tw, F1, rho2, S, err, st);
+      if (I) return launch_row3<T, LG, true>(image, I, sp, tw, F1, rho2, S, err, beam, st);
+      return launch_row3<T, LG, false>(image, I, sp, tw, F1, rho2, S, err, beam, st);
     }
-    return row3_switch<T, LG + 1>(lg, image, I, sp, tw, F1, rho2, S, err, st);
+    return row3_switch<T, LG + 1>(lg, image, I, sp, tw, F1, rho2, S, err, beam, st);
   }
 }
 
@@ -80,12 +81,12 @@ template <typename T> constexpr int col3_max_lg() { return sizeof(T) == 4 ? 13 :
 
 template <typename T, int LG>
 cudaError_t col3_switch(int lg, const void* F1, void* Gw, const void* tw, const double* rho2,
-                        double S, int kc_hint, cudaStream_t st) {
+                        double S, int kc_hint, bool full, cudaStream_t st) {
   if constexpr (LG > col3_max_lg<T>()) {
     return cudaErrorNotSupported;
   } else {
-    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, st);
-    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, st);
+    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, full, st);
+    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, full, st);
   }
 }
 
@@ -97,16 +98,17 @@ inline int ilog2i(int n) {
 
 template <typename T>
 cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
-                     void* F1, const double* rho2, double S, int* err, cudaStream_t st) {
+                     void* F1, const double* rho2, double S, int* err, const T* beam,
+                     cudaStream_t st) {
   constexpr int LG0 = ilog2c(FftV<T>::V);
-  return row3_switch<T, LG0>(ilog2i(N / 2), image, I, sp, tw, F1, rho2, S, err, st);
+  return row3_switch<T, LG0>(ilog2i(N / 2), image, I, sp, tw, F1, rho2, S, err, beam, st);
 }
 
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, cudaStream_t st) {
+                     int kc_hint, bool full, cudaStream_t st) {
   constexpr int LG0 = ilog2c(FftV<T>::V);
-  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, st);
+  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, full, st);
 }
 
 }  // namespace gal

@@ -50,19 +50,43 @@ template <typename T> struct Launch {
                               cudaStream_t st);
   static cudaError_t sweep(const T* I, const SweepParams& sp, int N, T* img, int blocks,
                            cudaStream_t st);
-  // err: bit 2 is set if a staged copy's wait timed out (never expected)
+  // err: bit 2 is set if a staged copy's wait timed out (never expected);
+  // beam: primary-beam tables of beam_table (null: no beam)
   static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                               const void* tw, void* F1, const double* rho2, double S, int* err,
-                              cudaStream_t st);
-  // kc_hint: kept columns if the host knows them (0: unknown)
+                              const T* beam, cudaStream_t st);
+  // primary-beam tables (2 N values) for a beam of FWHM fwhm > 0 on the
+  // pointing centre, seen from a model moved by (dRA, dDec) at position angle PA
+  static cudaError_t beam_table(T* tab, int N, double dxy, double fwhm, double dRA, double dDec,
+                                double PA, cudaStream_t st);
+  // kc_hint: window columns if the host knows them (0: unknown); full: the
+  // full-plane window of full_cols (lengths of the compile-time passes only)
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
-                              const double* rho2, double S, int kc_hint, cudaStream_t st);
+                              const double* rho2, double S, int kc_hint, bool full,
+                              cudaStream_t st);
   // ms: multi-source offsets (null: the single offset of gp)
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
                             int64_t M, void* vis, double* partials, unsigned* counter,
                             double* chi2, size_t window_smem, bool edge, int blocks,
                             const MultiSources* ms, cudaStream_t st);
+};
+
+// Full-plane (complex-to-complex) spectrum path (gal_plane.cuh), instantiated
+// per precision in gal_plane_f32.cu / gal_plane_f64.cu.  F1 then holds W =
+// full_cols(bounds, N).W columns and the window nrw x W nodes; the column
+// pass runs with full = true.
+template <typename T> struct Plane {
+  static bool supported(int N);  // transform lengths of the full-plane row pass
+  static cudaError_t rows(const T* image, const T* I, const SweepParams& sp, int N,
+                          const void* tw, void* F1, const double* rho2, double S, const T* beam,
+                          cudaStream_t st);
+  static int gather_blocks_per_sm(bool chi2, size_t window_smem);
+  static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
+                            const T* u, const T* v, const T* re, const T* im, const T* w,
+                            int64_t M, void* vis, double* partials, unsigned* counter,
+                            double* chi2, size_t window_smem, bool edge, int blocks,
+                            cudaStream_t st);
 };
 
 // Requests per launch of the batched passes (their job arrays are kernel
@@ -118,9 +142,10 @@ template <typename T> struct BatchLaunch {
 // the length is outside their range (the caller then uses the generic passes).
 template <typename T>
 cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
-                     void* F1, const double* rho2, double S, int* err, cudaStream_t st);
+                     void* F1, const double* rho2, double S, int* err, const T* beam,
+                     cudaStream_t st);
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, cudaStream_t st);
+                     int kc_hint, bool full, cudaStream_t st);
 
 }  // namespace gal

@@ -193,6 +193,39 @@ __global__ void sweep_kernel(const T* __restrict__ I, SweepT<T> p, int N, T* __r
   }
 }
 
+// Primary-beam tables (Sect. 2.1: A is the antenna pattern normalised at the
+// pointing centre, its central lobe a Gaussian of full width at half maximum
+// K lambda / D): A(s) = exp(-c |s|^2), c = 4 ln 2 / fwhm^2, fixed on the
+// phase centre.  After the PA rotation and the move o = (dRA, dDec) of
+// Sect. 3.2, model pixel p = (x_j, y_i) lies on the sky at s = R^T p + o, and
+// |R^T p + o| = |p + R o|, so A splits into a column term exp(-c (x_j + bx)^2)
+// and a row term exp(-c (y_i + by)^2) with (bx, by) = R o.  Entry n < N is the
+// column term of shifted column n (image column (n + N/2) mod N), entry N + n
+// the row term of shifted row n; both in FP64, rounded once to T.
+template <typename T>
+__global__ void beam_table_kernel(T* __restrict__ tab, int N, double dxy, double c, double bx,
+                                  double by) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 2 * N) return;
+  const int n = q < N ? q : q - N;
+  const int j = (n + N / 2) & (N - 1);
+  const double s = (double)(N / 2 - j) * dxy + (q < N ? bx : by);
+  tab[q] = (T)exp(-c * s * s);
+}
+
+// Primary-beam factor (Sect. 2.1: the visibility is the transform of A I).
+// The beam is a separable Gaussian on the image grid (see beam_table_kernel),
+// tabulated in the fftshifted index order of the row pass: beam[n] for
+// shifted column n, beam[N + i'] for shifted row i'.  A row-pass thread holds
+// pixel pairs (2n, 2n + 1) of shifted row i' as one complex value.
+template <typename T>
+__device__ __forceinline__ cplx_t<T> beam_pair(cplx_t<T> z, const T* __restrict__ beam, int N,
+                                               int row, int n) {
+  const T ay = __ldg(beam + N + row);
+  const cplx_t<T> ax = __ldg(reinterpret_cast<const cplx_t<T>*>(beam) + n);
+  return mkc(z.x * (ay * ax.x), z.y * (ay * ax.y));
+}
+
 // ---------------------------------------------------------------------------
 // Row pass.  F1 row i' (i' = 0..N-1) is the real-to-complex FFT of row i' of
 // fftshift(image), i.e. of image row (i' + N/2) mod N with its two halves
@@ -207,7 +240,7 @@ template <typename T, bool SWEEP>
 __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ image, const T* __restrict__ I,
                                 SweepT<T> sp, int N, const cplx_t<T>* __restrict__ tw,
                                 cplx_t<T>* __restrict__ F1, const double* __restrict__ rho2,
-                                double S) {
+                                double S, const T* __restrict__ beam) {
   using C = cplx_t<T>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
@@ -230,6 +263,7 @@ __global__ void __launch_bounds__(1024) row_pass_kernel(const T* __restrict__ im
       } else {
         z = *reinterpret_cast<const C*>(image + (size_t)irow * N + j);
       }
+      if (beam) z = beam_pair(z, beam, N, row, n);
       s[n] = z;
     }
   }
@@ -346,6 +380,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
   C* __restrict__ F1 = jb.F1;
   const double* __restrict__ rho2 = jb.rho2;
   const double S = jb.S;
+  const T* __restrict__ beam = jb.beam;
   constexpr int M = 1 << LG, N = 2 * M;
   using SH = Shape3<T, M, N>;
   using P = typename SH::P;
@@ -438,6 +473,10 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       C v[V];
 #pragma unroll
       for (int r = 0; r < V; ++r) v[r] = slot[t + r * TT];
+      if (beam) {
+#pragma unroll
+        for (int r = 0; r < V; ++r) v[r] = beam_pair(v[r], beam, N, grp * G + g, t + r * TT);
+      }
       // stage 0 writes the work buffer; the slot is reused from stage 1 on,
       // after the barrier that ends stage 0
       transform(v, work + (size_t)g * RS, slot, grp * G + g);
@@ -458,6 +497,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
         v[r] = mkc(sweep_pixel(I, sp, N, irow, j), sweep_pixel(I, sp, N, irow, j + 1));
       else
         v[r] = *reinterpret_cast<const C*>(image + (size_t)irow * N + j);
+      if (beam) v[r] = beam_pair(v[r], beam, N, row, n);
     }
     transform(v, A, B, row);
   }
@@ -486,6 +526,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   C* base = reinterpret_cast<C*>(smem_raw);
   const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
   const Bounds bd = block_bounds(rho2, S, N);
+  const int ncol = jb.full ? full_cols(bd, N).W : bd.Kc;  // window columns (and pitch)
   C tw1[V - 1];
   load_tw1<N, V, 1>(tw1, t, tw);
   const int kmax = N / 2 - bd.r0;
@@ -497,9 +538,9 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   C* B = base + (size_t)(G + g) * RS;
   auto sync = [] { __syncthreads(); };
   grid_dep_wait();  // F1 is the row pass's output
-  for (int c0 = blockIdx.x * G; c0 < bd.Kc; c0 += gridDim.x * G) {
+  for (int c0 = blockIdx.x * G; c0 < ncol; c0 += gridDim.x * G) {
     const int c = c0 + g;
-    const bool act = c < bd.Kc;
+    const bool act = c < ncol;
     C v[V];
 #pragma unroll
     for (int r = 0; r < V; ++r) v[r] = act ? F1[(size_t)c * N + t + r * TT] : mkc((T)0, (T)0);
@@ -516,8 +557,8 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
           pruned_pair3<N, V>(in, j, tj, xj, xmj);
         }
         if (act) {
-          Gw[(size_t)(kmax + j) * bd.Kc + c] = xj;
-          if (j > 0) Gw[(size_t)(kmax - j) * bd.Kc + c] = xmj;
+          Gw[(size_t)(kmax + j) * ncol + c] = xj;
+          if (j > 0) Gw[(size_t)(kmax - j) * ncol + c] = xmj;
         }
       }
     } else {
@@ -527,7 +568,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
       __syncthreads();
       if (act)
         for (int rr = t; rr < bd.nrw; rr += TT)
-          Gw[(size_t)rr * bd.Kc + c] = o[pad3<V>((bd.r0 + rr + N / 2) & (N - 1))];
+          Gw[(size_t)rr * ncol + c] = o[pad3<V>((bd.r0 + rr + N / 2) & (N - 1))];
     }
     __syncthreads();
   }
@@ -549,6 +590,7 @@ struct Window {
   int cmax;   // last cell column, Kc - 2
   int rmax;   // last cell row, nrw - 2
   int rofs;   // N/2 - r0: window row of v = 0
+  int cofs;   // window column of u = 0 (0 for the half spectrum)
   unsigned amax;  // node index of the last cell's first node, rmax * pitch + cmax
 };
 __device__ __forceinline__ Window make_window(const Bounds& b, int N) {
@@ -557,6 +599,19 @@ __device__ __forceinline__ Window make_window(const Bounds& b, int N) {
   w.cmax = b.Kc - 2;
   w.rmax = b.nrw - 2;
   w.rofs = N / 2 - b.r0;
+  w.cofs = 0;
+  w.amax = (unsigned)(w.rmax * w.pitch + w.cmax);
+  return w;
+}
+// the full-plane window: both signs of u (full_cols), no fold
+__device__ __forceinline__ Window make_window_full(const Bounds& b, int N) {
+  const FullCols f = full_cols(b, N);
+  Window w;
+  w.pitch = f.W;
+  w.cmax = f.W - 2;
+  w.rmax = b.nrw - 2;
+  w.rofs = N / 2 - b.r0;
+  w.cofs = f.lo;
   w.amax = (unsigned)(w.rmax * w.pitch + w.cmax);
   return w;
 }
@@ -606,12 +661,14 @@ template <typename T> struct RowJob {
   cplx_t<T>* F1;        // row-pass output, column-major (Kc columns of N)
   const double* rho2;   // squared uv extent of the request's points
   double S;             // nxy * dxy
+  const T* beam;        // primary-beam factors (beam_table_kernel), null: none
 };
 template <typename T> struct ColJob {
   const cplx_t<T>* F1;
-  cplx_t<T>* Gw;        // window output, nrw x Kc
+  cplx_t<T>* Gw;        // window output, nrw x Kc (full plane: nrw x W)
   const double* rho2;
   double S;
+  int full;             // 1: the full-plane window (full_cols(bd, N).W columns)
 };
 
 template <> struct GatherT<double> {
@@ -741,7 +798,7 @@ __device__ __forceinline__ float phase_turns(float u, float v, ff PX, ff PY) {
   return f - rintf(f);
 }
 
-template <bool SMEM, bool EDGE, bool MULTI = false>
+template <bool SMEM, bool EDGE, bool MULTI = false, bool FULL = false>
 __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__ Gp, const Window& w,
                                                const GatherT<float>& p, float u, float v,
                                                const MultiPhase<float>* mp = nullptr) {
@@ -755,7 +812,8 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
   float yh = ya + yb;
   t = yh - ya;
   float yl = ((ya - (yh - t)) + (yb - t)) + (yae + ybe);
-  const bool neg = xh < 0.f;  // Hermitian fold: use (-u', -v') and conjugate
+  // Hermitian fold (half spectrum only): use (-u', -v') and conjugate
+  const bool neg = !FULL && xh < 0.f;
   if (neg) {
     xh = -xh;
     xl = -xl;
@@ -768,10 +826,13 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
   const float cf = floorf(xh), rf = floorf(yh);
   float fu = __saturatef((xh - cf) + xl);
   float fv = __saturatef((yh - rf) + yl);
-  int c = (int)fminf(cf, 32768.f);
+  int c = FULL ? (int)fmaxf(fminf(cf, 32768.f), -32768.f) + w.cofs : (int)fminf(cf, 32768.f);
   int r = (int)fmaxf(fminf(rf, 32768.f), -32768.f) + w.rofs;
   if constexpr (EDGE) {
-    if (c > w.cmax) {
+    if (FULL && c < 0) {
+      c = 0;
+      fu = 0.f;
+    } else if (c > w.cmax) {
       c = w.cmax;
       fu = 1.f;
     }
@@ -879,19 +940,22 @@ __device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 m1, float2
   return s;
 }
 
-template <bool SMEM, bool EDGE>
+template <bool SMEM, bool EDGE, bool FULL = false>
 __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const Window& w, float xh,
                                            float xl, float yh, float yl, bool neg, float2& V) {
   // positions are grid offsets (|.| <= 8192), so the FMA-pipe floor applies;
   // non-finite input yields an arbitrary cell, clamped below, and NaN through
   // the phase
   float cf, rf;
-  int c = floor_fma(xh, cf);
+  int c = floor_fma(xh, cf) + (FULL ? w.cofs : 0);
   int r = floor_fma(yh, rf) + w.rofs;
   float fu = __saturatef((xh - cf) + xl);
   float fv = __saturatef((yh - rf) + yl);
   if constexpr (EDGE) {
-    if (c > w.cmax) {
+    if (FULL && c < 0) {
+      c = 0;
+      fu = 0.f;
+    } else if (c > w.cmax) {
       c = w.cmax;
       fu = 1.f;
     }
@@ -925,7 +989,7 @@ __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const W
 // is exact, plus the low part.  Non-finite input gives an arbitrary node
 // index, clamped so every read stays in the window (its result is NaN
 // through the phase).
-template <bool SMEM>
+template <bool SMEM, bool FULL = false>
 __device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, const Window& w,
                                                  float2 xh, float2 xl, float2 yh, float2 yl,
                                                  float2 m1, float2& A0, float2& A1) {
@@ -936,7 +1000,7 @@ __device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, c
   constexpr int kMagicBits = 0x4B400000;  // bit pattern of 1.5 2^23
   auto node = [&](float t_x, float t_y) {
     const int r = __float_as_int(t_y) - kMagicBits + w.rofs;
-    const int c = __float_as_int(t_x) - kMagicBits;
+    const int c = __float_as_int(t_x) - kMagicBits + (FULL ? w.cofs : 0);
     return min((unsigned)(r * w.pitch + c), w.amax);
   };
   auto lerp = [&](unsigned a, float f_u, float f_v) {
@@ -966,7 +1030,7 @@ __device__ __forceinline__ float2 phase_turns2(float2 U, float2 Vv, float2 PXh, 
   return fma2(rint_fma2(f), m1, f);
 }
 
-template <bool SMEM, bool EDGE, bool MULTI = false>
+template <bool SMEM, bool EDGE, bool MULTI = false, bool FULL = false>
 __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const Window& w,
                                             const Pair2Const& k, float2 U, float2 Vv, float2& V0,
                                             float2& V1, const MultiPhase<float>* mp = nullptr) {
@@ -1005,18 +1069,27 @@ __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const 
     __sincosf(ang.x, &s0, &c0);
     __sincosf(ang.y, &s1, &c1);
   }
-  // Hermitian fold per lane
-  const bool n0 = xh2.x < 0.f, n1 = xh2.y < 0.f;
-  const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
-  const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
   float2 A0, A1;
-  if constexpr (EDGE) {
-    cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
-    cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
+  if constexpr (FULL) {  // full plane: both signs of u are in the window
+    if constexpr (EDGE) {
+      cell_fetch<SMEM, EDGE, true>(G, w, xh2.x, xl2.x, yh2.x, yl2.x, false, A0);
+      cell_fetch<SMEM, EDGE, true>(G, w, xh2.y, xl2.y, yh2.y, yl2.y, false, A1);
+    } else {
+      cell_pair_pruned<SMEM, true>(G, w, xh2, xl2, yh2, yl2, k.m1, A0, A1);
+    }
   } else {
-    cell_pair_pruned<SMEM>(G, w, xh, xl, yh, yl, k.m1, A0, A1);
-    if (n0) A0.y = -A0.y;
-    if (n1) A1.y = -A1.y;
+    // Hermitian fold per lane
+    const bool n0 = xh2.x < 0.f, n1 = xh2.y < 0.f;
+    const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
+    const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
+    if constexpr (EDGE) {
+      cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
+      cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
+    } else {
+      cell_pair_pruned<SMEM>(G, w, xh, xl, yh, yl, k.m1, A0, A1);
+      if (n0) A0.y = -A0.y;
+      if (n1) A1.y = -A1.y;
+    }
   }
   // rotate by the phase: V (c + i s) = c V + s (-Vi, Vr)
   V0 = fma2(pk(s0, s0), pk(-A0.y, A0.x), mul2(pk(c0, c0), A0));
@@ -1040,7 +1113,7 @@ __device__ __forceinline__ void cell_d(double x, int ofs, int last, int& c, doub
   }
 }
 
-template <bool SMEM, bool EDGE, bool MULTI = false>
+template <bool SMEM, bool EDGE, bool MULTI = false, bool FULL = false>
 __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict__ Gp, const Window& w,
                                                 const GatherT<double>& p, double u, double v,
                                                 const MultiPhase<double>* mp = nullptr) {
@@ -1048,7 +1121,7 @@ __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict
     return make_double2(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
   double up = u * p.cpa - v * p.spa;
   double vp = u * p.spa + v * p.cpa;
-  const bool neg = up < 0.0;
+  const bool neg = !FULL && up < 0.0;  // Hermitian fold (half spectrum only)
   if (neg) {
     up = -up;
     vp = -vp;
@@ -1056,7 +1129,7 @@ __device__ __forceinline__ double2 sample_point(const cplx_t<double>* __restrict
   int r, c;
   double fr, fc;
   cell_d(vp * p.S, w.rofs, w.rmax, r, fr);
-  cell_d(up * p.S, 0, w.cmax, c, fc);
+  cell_d(up * p.S, FULL ? w.cofs : 0, w.cmax, c, fc);
   const double2* g = Gp + (size_t)r * w.pitch + c;
   const double2 g00 = ld_node<SMEM>(g), g01 = ld_node<SMEM>(g + 1);
   const double2 g10 = ld_node<SMEM>(g + w.pitch), g11 = ld_node<SMEM>(g + w.pitch + 1);
@@ -1173,7 +1246,7 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
 
 // Loop over this thread's uv points, reading the window nodes through G
 // (SMEM: G points into shared memory).
-template <typename T, bool CHI2, bool SMEM, bool EDGE, bool MULTI, typename ACC>
+template <typename T, bool CHI2, bool SMEM, bool EDGE, bool MULTI, bool FULL, typename ACC>
 __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
                                               const GatherT<T>& p, const T* __restrict__ u,
                                               const T* __restrict__ v, const T* __restrict__ re,
@@ -1182,7 +1255,9 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
                                               ACC& acc, const MultiPhase<T>* mp) {
   using C = cplx_t<T>;
   constexpr int W = Vec16<T>::W;
-  auto point = [&](T uu, T vv) { return sample_point<SMEM, EDGE, MULTI>(G, win, p, uu, vv, mp); };
+  auto point = [&](T uu, T vv) {
+    return sample_point<SMEM, EDGE, MULTI, FULL>(G, win, p, uu, vv, mp);
+  };
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = vec ? M / W : 0;
@@ -1206,7 +1281,7 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
       for (int e = 0; e < W; e += 2)
-        sample_pair<SMEM, EDGE, MULTI>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]),
+        sample_pair<SMEM, EDGE, MULTI, FULL>(G, win, p, pk(uu[e], uu[e + 1]), pk(vv[e], vv[e + 1]),
                                        Vs[e], Vs[e + 1], mp);
     } else {
 #pragma unroll
@@ -1244,7 +1319,7 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 // final reduction overlap the other's stream), 256-thread blocks otherwise
 template <bool SMEM> constexpr int gather_threads() { return SMEM ? 512 : 256; }
 
-template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false>
+template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false, bool FULL = false>
 __global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 2 : 3)
 gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes,
               const __grid_constant__ MultiArg<T, MULTI> multi) {
@@ -1266,7 +1341,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
   unsigned* __restrict__ counter = jb.counter;
   double* __restrict__ chi2_out = jb.chi2_out;
   const Bounds bd = block_bounds(rho2, p.Sd, p.N);
-  const Window win = make_window(bd, p.N);
+  const Window win = FULL ? make_window_full(bd, p.N) : make_window(bd, p.N);
   typename Acc<T>::type acc;
   // the observation does not depend on the column pass: pull this thread's
   // first group towards L2 while that pass finishes
@@ -1287,7 +1362,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
   if constexpr (SMEM) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     C* sw = reinterpret_cast<C*>(smem_raw);
-    const int nodes = bd.nrw * bd.Kc;
+    const int nodes = bd.nrw * win.pitch;
     if (nodes <= smem_nodes) {  // uniform over the grid; always true when sized by the host
       // one bulk copy of the window (rounded up to 16 bytes; the window
       // buffer and the shared allocation both have the slack)
@@ -1305,7 +1380,8 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
         for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
         __syncthreads();
       }
-      gather_points<T, CHI2, true, EDGE, MULTI>(sw, win, p, u, v, re, im, w, M, vec, vis, acc, mp);
+      gather_points<T, CHI2, true, EDGE, MULTI, FULL>(sw, win, p, u, v, re, im, w, M, vec, vis, acc,
+                                                      mp);
     } else {
       // the host sizes the shared window from the same extent, so this is
       // never taken; the result is NaN rather than a read out of bounds
@@ -1319,7 +1395,8 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
       }
     }
   } else {
-    gather_points<T, CHI2, false, EDGE, MULTI>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc, mp);
+    gather_points<T, CHI2, false, EDGE, MULTI, FULL>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc,
+                                                     mp);
   }
   if constexpr (CHI2) {
     __shared__ double ws[32];
@@ -1502,12 +1579,12 @@ cudaError_t Launch<T>::sweep(const T* I, const SweepParams& sp, int N, T* img, i
 template <typename T>
 cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                                 const void* tw, void* F1, const double* rho2, double S, int* err,
-                                cudaStream_t st) {
+                                const T* beam, cudaStream_t st) {
   using C = cplx_t<T>;
   const int M = N / 2;
   const bool al16 = I || (reinterpret_cast<uintptr_t>(image) & 15u) == 0;
   if (M >= FftV<T>::V && al16) {
-    const cudaError_t e = row_fft3<T>(image, I, sp, N, tw, F1, rho2, S, err, st);
+    const cudaError_t e = row_fft3<T>(image, I, sp, N, tw, F1, rho2, S, err, beam, st);
     if (e != cudaErrorNotSupported) return e;
   }
   const C* twc = static_cast<const C*>(tw);
@@ -1521,21 +1598,33 @@ cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& s
   const int grid = (N + rpb - 1) / rpb;
   if (I)
     row_pass_kernel<T, true><<<grid, threads, smem, st>>>(nullptr, I, sweep_cast<T>(sp), N, twc,
-                                                           out, rho2, S);
+                                                           out, rho2, S, beam);
   else
     row_pass_kernel<T, false><<<grid, threads, smem, st>>>(image, nullptr, SweepT<T>{}, N, twc,
-                                                            out, rho2, S);
+                                                            out, rho2, S, beam);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::beam_table(T* tab, int N, double dxy, double fwhm, double dRA, double dDec,
+                                  double PA, cudaStream_t st) {
+  const double c = 4.0 * std::log(2.0) / (fwhm * fwhm);
+  const double cp = std::cos(PA), sp = std::sin(PA);
+  const double bx = dRA * cp - dDec * sp, by = dRA * sp + dDec * cp;  // R (dRA, dDec)
+  beam_table_kernel<T><<<(2 * N + 255) / 256, 256, 0, st>>>(tab, N, dxy, c, bx, by);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::col_pass(const void* F1, void* Gw, int N, const void* tw,
-                                const double* rho2, double S, int kc_hint, cudaStream_t st) {
+                                const double* rho2, double S, int kc_hint, bool full,
+                                cudaStream_t st) {
   using C = cplx_t<T>;
   if (N >= FftV<T>::V) {
-    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, st);
+    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, full, st);
     if (e != cudaErrorNotSupported) return e;
   }
+  if (full) return cudaErrorNotSupported;  // the generic pass keeps the half plane only
   const int P = N / 2 + 1;
   const int tg = col_threads_per_col(N);
   int cpb = 256 / tg;

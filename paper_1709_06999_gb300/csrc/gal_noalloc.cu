@@ -111,9 +111,9 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
     return GAL_E_CUDA;
   const double S = (double)nxy * dxy;
   gal::SweepParams none{};
-  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, cs) != cudaSuccess)
+  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, nullptr, cs) != cudaSuccess)
     return GAL_E_CUDA;
-  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, 0, cs) != cudaSuccess)
+  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, 0, false, cs) != cudaSuccess)
     return GAL_E_CUDA;
   gal::GatherParams gp;
   gp.cpa = std::cos(PA);

@@ -1,0 +1,214 @@
+// Full-plane (complex-to-complex) spectrum path: the row pass transforms each
+// real image row as a complex sequence of length N, keeps both signs of u,
+// and the gather samples the window without the Hermitian fold.  The paper
+// checks this transform against the real-to-complex one (Sect. 5); here it is
+// an alternative spectrum path with its own kernels, and the primary-beam
+// factor (Sect. 2.1) applies to it as to the half-plane path.
+#pragma once
+
+#include "gal_fft3_launch.cuh"
+
+namespace gal {
+
+// Longest full-plane transform: both ping-pong buffers of one row in shared
+// memory, as for the column pass (8192 float2, 4096 double2).
+template <typename T> constexpr int plane_max_lg() { return col3_max_lg<T>(); }
+
+// Row i' of F1 (column-major) holds, for u bins k = -lo .. hi of full_cols()
+// (column k + lo), bin k mod N of the length-N complex FFT of row i' of
+// fftshift(image) taken as x + 0i, i.e. of image row (i' + N/2) mod N with
+// its halves swapped.  Pruned, X[j] and X[N - j] come from one evaluation of
+// the last stage (pruned_pair3); otherwise the whole transform is kept.
+// The beam tables, when given, multiply each pixel as in the half-plane pass.
+template <typename T, int LG, bool SWEEP>
+__global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads,
+                                  min_blocks_128regs<Shape3<T, (1 << LG), (1 << 30)>::threads>())
+row_c2c_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __restrict__ tw) {
+  using C = cplx_t<T>;
+  grid_dep_launch();  // the column pass may be scheduled as our blocks retire
+  constexpr int N = 1 << LG;
+  using SH = Shape3<T, N, (1 << 30)>;
+  using P = typename SH::P;
+  constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* base = reinterpret_cast<C*>(smem_raw);
+  const int g = threadIdx.x / TT, t = threadIdx.x - g * TT;
+  const Bounds bd = block_bounds(jb.rho2, jb.S, N);
+  const FullCols fc = full_cols(bd, N);
+  const int kmax = fc.lo > fc.hi ? fc.lo : fc.hi;
+  C tw1[V - 1];
+  load_tw1<N, V, 1>(tw1, t, tw);
+  const bool pruned = P::nstage >= 2 && kmax < P::Nsl;
+  const bool one_j = kmax < TT;
+  C twp[V];
+  if (pruned && one_j && t <= kmax) load_twp<N, V, 1>(twp, t, tw);
+  C* A = base + (size_t)g * RS;
+  C* B = base + (size_t)(G + g) * RS;
+  auto sync = [] { __syncthreads(); };
+  const T* __restrict__ beam = jb.beam;
+  C* __restrict__ F1 = jb.F1;
+  for (int r0 = blockIdx.x * G; r0 < N; r0 += gridDim.x * G) {
+    const int row = r0 + g;
+    const bool act = row < N;
+    const int irow = (row + N / 2) & (N - 1);
+    C v[V];
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+      const int n = t + r * TT;
+      const int j = (n + N / 2) & (N - 1);
+      T x = (T)0;
+      if (act) {
+        if constexpr (SWEEP)
+          x = sweep_pixel(jb.I, jb.sp, N, irow, j);
+        else
+          x = jb.image[(size_t)irow * N + j];
+        if (beam) x = x * (__ldg(beam + N + row) * __ldg(beam + n));
+      }
+      v[r] = mkc(x, (T)0);
+    }
+    Head3<N, V, 1, 0>::run(v, A, B, t, tw, tw1, sync);
+    C* in = last_input<N, V>(A, B);
+    if (pruned) {
+      for (int j = t; j <= kmax; j += TT) {
+        C xj, xmj;
+        if (one_j) {
+          pruned_pair3<N, V>(in, j, twp, xj, xmj);
+        } else {
+          C tj[V];
+          load_twp<N, V, 1>(tj, j, tw);
+          pruned_pair3<N, V>(in, j, tj, xj, xmj);
+        }
+        if (act) {
+          if (j <= fc.hi) F1[(size_t)(fc.lo + j) * N + row] = xj;
+          if (j > 0 && j <= fc.lo) F1[(size_t)(fc.lo - j) * N + row] = xmj;
+        }
+      }
+    } else {
+      last_full<N, V, 1>(v, in, t, tw);
+      C* o = in == A ? B : A;
+      store_full<N, V>(v, o, t);
+      __syncthreads();
+      if (act)
+        for (int cc = t; cc < fc.W; cc += TT) F1[(size_t)cc * N + row] = o[pad3<V>((cc - fc.lo) & (N - 1))];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int LG, bool SWEEP>
+cudaError_t launch_row_c2c(const RowJob<T>& jb, const void* tw, cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int N = 1 << LG;
+  using SH = Shape3<T, N, (1 << 30)>;
+  constexpr auto kern = row_c2c_kernel<T, LG, SWEEP>;
+  const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
+  cudaError_t e = ensure_smem_attr<kern>(smem);
+  if (e) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+  if (e) return e;
+  if (per_sm < 1) per_sm = 1;
+  int grid = per_sm * current_device_sms();
+  const int need = (N + SH::G - 1) / SH::G;
+  if (grid > need) grid = need;
+  kern<<<grid, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw));
+  return cudaGetLastError();
+}
+
+template <typename T, int LG>
+cudaError_t row_c2c_switch(int lg, const RowJob<T>& jb, bool sweep, const void* tw,
+                           cudaStream_t st) {
+  if constexpr (LG > plane_max_lg<T>()) {
+    return cudaErrorNotSupported;
+  } else {
+    if (lg == LG)
+      return sweep ? launch_row_c2c<T, LG, true>(jb, tw, st) : launch_row_c2c<T, LG, false>(jb, tw, st);
+    return row_c2c_switch<T, LG + 1>(lg, jb, sweep, tw, st);
+  }
+}
+
+template <typename T> bool Plane<T>::supported(int N) {
+  return N >= FftV<T>::V && N <= (1 << plane_max_lg<T>()) && (N & (N - 1)) == 0;
+}
+
+template <typename T>
+cudaError_t Plane<T>::rows(const T* image, const T* I, const SweepParams& sp, int N,
+                           const void* tw, void* F1, const double* rho2, double S, const T* beam,
+                           cudaStream_t st) {
+  if (!supported(N)) return cudaErrorNotSupported;
+  RowJob<T> jb{image, I, I ? sweep_cast<T>(sp) : SweepT<T>{}, static_cast<cplx_t<T>*>(F1), rho2, S,
+               beam};
+  constexpr int LG0 = ilog2c(FftV<T>::V);
+  return row_c2c_switch<T, LG0>(ilog2i(N), jb, I != nullptr, tw, st);
+}
+
+template <typename T> int Plane<T>::gather_blocks_per_sm(bool chi2, size_t window_smem) {
+  int n = 0;
+  if (window_smem) {
+    if (chi2) {
+      constexpr auto kern = gather_kernel<T, true, true, true, 1, false, true>;
+      if (ensure_smem_attr<kern>(window_smem) == cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true>(), window_smem);
+    } else {
+      constexpr auto kern = gather_kernel<T, false, true, true, 1, false, true>;
+      if (ensure_smem_attr<kern>(window_smem) == cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true>(), window_smem);
+    }
+  } else {
+    if (chi2)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &n, gather_kernel<T, true, false, true, 1, false, true>, gather_threads<false>(), 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &n, gather_kernel<T, false, false, true, 1, false, true>, gather_threads<false>(), 0);
+  }
+  (void)cudaGetLastError();
+  return n < 1 ? 1 : n;
+}
+
+template <typename T>
+cudaError_t Plane<T>::gather(const void* Gw, const GatherParams& gp, const double* rho2,
+                             const T* u, const T* v, const T* re, const T* im, const T* w,
+                             int64_t M, void* vis, double* partials, unsigned* counter,
+                             double* chi2, size_t window_smem, bool edge, int blocks,
+                             cudaStream_t st) {
+  using C = cplx_t<T>;
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  int vec = al16(u) && al16(v);
+  if (chi2) vec = vec && al16(re) && al16(im) && al16(w);
+  const int nodes = (int)(window_smem / sizeof(C));
+  const int threads = window_smem ? gather_threads<true>() : gather_threads<false>();
+  int grid = blocks;
+  if (!chi2) {
+    int64_t need = (M + threads - 1) / threads;
+    if (need < 1) need = 1;
+    if (need < grid) grid = (int)need;
+  }
+  Jobs<GatherJob<T>, 1> jb;
+  jb.j[0] = GatherJob<T>{static_cast<const C*>(Gw), GatherT<T>::make(gp), rho2, u, v, re, im, w, M,
+                         vec, static_cast<C*>(vis), partials, counter, chi2};
+  cudaError_t le = cudaSuccess;
+  auto pick = [&](auto chi2_c, auto smem_c, auto edge_c) {
+    constexpr bool CH = decltype(chi2_c)::value, SM = decltype(smem_c)::value,
+                   ED = decltype(edge_c)::value;
+    constexpr auto kern = gather_kernel<T, CH, SM, ED, 1, false, true>;
+    const size_t smem = SM ? window_smem : 0;
+    le = ensure_smem_attr<kern>(smem);
+    if (le == cudaSuccess)
+      le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes,
+                            MultiArg<T, false>{});
+  };
+  using TT = std::true_type;
+  using FF = std::false_type;
+  if (chi2) {
+    if (window_smem) edge ? pick(TT{}, TT{}, TT{}) : pick(TT{}, TT{}, FF{});
+    else edge ? pick(TT{}, FF{}, TT{}) : pick(TT{}, FF{}, FF{});
+  } else {
+    if (window_smem) edge ? pick(FF{}, TT{}, TT{}) : pick(FF{}, TT{}, FF{});
+    else edge ? pick(FF{}, FF{}, TT{}) : pick(FF{}, FF{}, FF{});
+  }
+  if (le != cudaSuccess) return le;
+  return cudaGetLastError();
+}
+
+}  // namespace gal

@@ -60,3 +60,15 @@ def test_create_without_gpu_fails_cleanly(lib):
         pytest.skip("a GPU is present")
     h = ct.c_void_p()
     assert lib.gal_create(ct.byref(h), 0) == -5
+
+
+def test_options_struct_layout():
+    """struct gal_opts { double pb_fwhm; int full_plane; }: the binding's
+    ctypes mirror has the C layout (8-byte double, int at offset 8, size 16)."""
+    import ctypes as ct
+    from paper_1709_06999_gb300._native import GalOpts
+    assert ct.sizeof(GalOpts) == 16
+    assert GalOpts.pb_fwhm.offset == 0 and GalOpts.full_plane.offset == 8
+    text = open(HEADER).read()
+    assert re.search(r"typedef struct gal_opts \{\s*double pb_fwhm;\s*int full_plane;\s*\} gal_opts;",
+                     text)
