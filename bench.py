@@ -40,20 +40,31 @@ NXY, M_UV = 4096, 5_000_000
 L2_FLUSH_BYTES = 256 << 20
 STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
 # kernels launched for this workload (template arguments as ncu prints them)
-KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1>", 2: "col_fft3_kernel<float, 12, 1>",
-           3: "gather_kernel<float, 1, 1, 0, 1, 0>"}
+KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1, 0>", 2: "col_fft3_kernel<float, 12, 1>",
+           3: "gather_kernel<float, 1, 1, 0, 1, 0, 0>"}
+# the full-plane (complex-to-complex) spectrum path
+KERNELS_FULL = {1: "row_c2c_kernel<float, 12, 0>", 2: "col_fft3_kernel<float, 12, 1>",
+                3: "gather_kernel<float, 1, 1, 0, 1, 0, 1>"}
+# primary beam of a 12 m antenna at 100 GHz: FWHM = K lambda / D, K = 1.13
+PB_FWHM = 1.13 * (299792458.0 / 100e9) / 12.0
+VARIANTS = {"plain": {}, "beam": {"pb_fwhm": PB_FWHM}, "full_plane": {"full_plane": True},
+            "beam_full_plane": {"pb_fwhm": PB_FWHM, "full_plane": True}}
 
 
-def algorithmic_bytes(stage: int, nxy: int, M: int, Kc: int, nrw: int) -> float:
-    """Compulsory DRAM bytes of one launch of a stage (float32 path).
+def algorithmic_bytes(stage: int, nxy: int, M: int, Kc: int, nrw: int,
+                      beam: bool = False) -> float:
+    """Compulsory DRAM bytes of one launch of a stage (float32 path); Kc is
+    the number of window columns (2 Kc - 1 of the half plane's Kc for the
+    full plane).
 
     row FFT:   read the image (4 N^2) + write the kept columns (8 N Kc)
+               (+ the beam tables, 2N floats, when a beam is applied)
     col FFT:   read the kept columns (8 N Kc) + write the window (8 nrw Kc)
     gather:    read u, v, Re, Im, w (20 B per point); the window (8 nrw Kc)
                is read once from DRAM and then served from cache
     """
     if stage == 1:
-        return 4.0 * nxy * nxy + 8.0 * nxy * Kc
+        return 4.0 * nxy * nxy + 8.0 * nxy * Kc + (8.0 * nxy if beam else 0.0)
     if stage == 2:
         return 8.0 * nxy * Kc + 8.0 * nrw * Kc
     if stage == 3:
@@ -72,9 +83,18 @@ def window(rho: float, S: float, N: int):
     return min(k + 1, P), hi - lo + 1
 
 
+def full_window_columns(Kc: int, N: int) -> int:
+    """Columns of the full-plane window (same rule as the library): u from
+    -(Kc-1) to Kc-1 when pruned, the node range -N/2 .. N/2-1 otherwise."""
+    lo = N // 2 if Kc >= N // 2 + 1 else Kc - 1
+    hi = min(Kc - 1, N // 2 - 1)
+    return lo + hi + 1
+
+
 # the sources that define the profiled kernels and their launch shapes
 KERNEL_SOURCES = ("gal_common.cuh", "gal_fft.cuh", "gal_fft2.cuh", "gal_fft3.cuh",
-                  "gal_fft3_launch.cuh", "gal_kernels.cuh", "gal_tma.cuh", "gal_internal.h")
+                  "gal_fft3_launch.cuh", "gal_kernels.cuh", "gal_plane.cuh", "gal_tma.cuh",
+                  "gal_internal.h")
 
 
 def kernel_source_hash() -> str:
@@ -274,6 +294,43 @@ def _single(ctx, r, out=None):
         return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, out=out)
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
                             r.PA, out=out)
+
+
+def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=200):
+    """chi2_image of the same workload with a primary beam, through the
+    full-plane spectrum, and both: L2 flushed before every step, each step
+    bracketed by events, plus per-stage times from three calibration steps."""
+    variants = {k: v for k, v in VARIANTS.items() if k != "plain"}
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, kw in variants.items():
+        for i in range(3):
+            ctx.chi2_image(img, dxy, obs, *params[i], out=out, **kw)
+        ctx.set_stage_timing(True)
+        for i in range(3):
+            flush_l2()
+            ctx.chi2_image(img, dxy, obs, *params[i], out=out, **kw)
+        cal = ctx.stage_times()
+        ctx.set_stage_timing(False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for i in range(steps):
+            flush_l2()
+            ev[i][0].record(stream)
+            ctx.chi2_image(img, dxy, obs, *params[i % len(params)], out=out, **kw)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        res[name] = {"value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms,
+                     "pb_fwhm_rad": kw.get("pb_fwhm", 0.0),
+                     "full_plane": bool(kw.get("full_plane", False)),
+                     "stages_us_per_step": {STAGES[s]: round(1000 * cal[s][0] / 3, 2)
+                                            for s in range(4) if cal[s][1]}}
+    res["note"] = ("same workload and timing as the headline step; per-stage times are sums "
+                   "per step over 3 calibration steps, each launch with about 4 us of event "
+                   "overhead; the beam-table launch belongs to the row stage")
+    return res
 
 
 def measure_batched(torch, ctx, dev, flush, reps=3):
@@ -478,9 +535,11 @@ def run_gpu(args):
               zip(prng.uniform(-0.1, 0.1, 8) * math.pi / 648000,
                   prng.uniform(-0.1, 0.1, 8) * math.pi / 648000, prng.uniform(0, math.pi, 8))]
 
+    opts = VARIANTS[args.variant]
+
     def step(i):
         dRA, dDec, PA = params[i % len(params)]
-        ctx.chi2_image(img, p.dxy, obs, dRA, dDec, PA, out=out)
+        ctx.chi2_image(img, p.dxy, obs, dRA, dDec, PA, out=out, **opts)
 
     def flush_l2():
         # write a buffer larger than L2 (evicts every line of the workload),
@@ -575,11 +634,15 @@ def run_gpu(args):
     # roofline of the dominant kernel (largest average launch time)
     rho = float(np.sqrt(np.max(p.u ** 2 + p.v ** 2)))
     Kc, nrw = window(rho, NXY * p.dxy, NXY)
+    full = bool(opts.get("full_plane", False))
+    kernels = KERNELS_FULL if full else KERNELS
+    if full:
+        Kc = full_window_columns(Kc, NXY)
     avg = {s: (stage[s][0] / stage[s][1]) for s in (1, 2, 3) if stage[s][1]}
-    alg = algorithmic_bytes(dom, NXY, M_UV, Kc, nrw)
+    alg = algorithmic_bytes(dom, NXY, M_UV, Kc, nrw, beam="pb_fwhm" in opts)
     achieved = alg / (avg[dom] * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic(KERNELS[dom])
+    traffic = measured_traffic(kernels[dom])
 
     base = None
     if world == 1 and args.cpu_evals > 0:
@@ -591,12 +654,13 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV, "l2": "flushed before every step (256 MiB write + 256 MiB read)",
-                   "kept_window": {"columns": Kc, "rows": nrw}, "parallelism": f"replicas x{world}"},
+                   "kept_window": {"columns": Kc, "rows": nrw}, "parallelism": f"replicas x{world}",
+                   "variant": args.variant},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * NXY * NXY,
                 "d2h_bytes_per_step": 8,
                 "note": "host image (pinned) -> device, chi2 -> host, per step; observation resident"},
         "gpu_launches": gpu_launches,
-        "roofline": {"bound": "hbm", "kernel": KERNELS[dom], "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kernels[dom], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes": alg,
                      "avg_launch_us": 1000 * avg[dom]},
@@ -612,6 +676,7 @@ def run_gpu(args):
     if base is not None:
         line["cpu_baseline"] = base
     if world == 1 and not args.no_extras:
+        line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out)
         line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
         line["serving"] = measure_serving(torch, dev)
     print(json.dumps(line), flush=True)
@@ -628,7 +693,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-evals", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched (cube, walkers) and serving measurements")
+                    help="skip the beam/full-plane, batched (cube, walkers) and serving "
+                         "measurements")
+    ap.add_argument("--variant", default="plain", choices=sorted(VARIANTS),
+                    help="options of the timed chi2_image step (plain: the headline line)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # the timing rules need at least 3 warm-up steps
     if args.impl == "reference":

@@ -6,37 +6,42 @@
 
 namespace gal {
 
+// A row pass with a beam follows beam_table_kernel in the stream and is
+// launched as its programmatic dependent (BEAM kernels wait for the tables).
+template <typename T, int LG, bool SWEEP, bool BEAM>
+cudaError_t launch_row3_kern(const Jobs<RowJob<T>, 1>& jb, const cplx_t<T>* twc, int* err,
+                             cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int M = 1 << LG, N = 2 * M;
+  using SH = Shape3<T, M, N>;
+  constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM>;
+  const size_t smem = 128 + (size_t)(SWEEP ? 2 : 3) * SH::G * SH::RS * sizeof(C);
+  cudaError_t e = ensure_smem_attr<kern>(smem);
+  if (e) return e;
+  int grid = N / SH::G;
+  if constexpr (!SWEEP) {  // persistent blocks over the TMA row ring
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+    if (e) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (grid > per_sm * current_device_sms()) grid = per_sm * current_device_sms();
+  }
+  if constexpr (BEAM) return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb, twc, err);
+  kern<<<grid, SH::threads, smem, st>>>(jb, twc, err);
+  return cudaGetLastError();
+}
+
 template <typename T, int LG, bool SWEEP>
 cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const void* tw,
                         void* F1, const double* rho2, double S, int* err, const T* beam,
                         cudaStream_t st) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LG, N = 2 * M;
-  using SH = Shape3<T, M, N>;
   const C* twc = static_cast<const C*>(tw);
-  C* out = static_cast<C*>(F1);
   Jobs<RowJob<T>, 1> jb;
-  jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, out, rho2, S, beam};
-  if constexpr (!SWEEP) {
-    constexpr auto kern = row_fft3_kernel<T, LG, true, false, 1>;
-    const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
-    cudaError_t e = ensure_smem_attr<kern>(smem);
-    if (e) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
-    if (e) return e;
-    if (per_sm < 1) per_sm = 1;
-    int grid = per_sm * current_device_sms();
-    if (grid > N / SH::G) grid = N / SH::G;
-    kern<<<grid, SH::threads, smem, st>>>(jb, twc, err);
-  } else {
-    constexpr auto kern = row_fft3_kernel<T, LG, false, true, 1>;
-    const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
-    const cudaError_t e = ensure_smem_attr<kern>(smem);
-    if (e) return e;
-    kern<<<N / SH::G, SH::threads, smem, st>>>(jb, twc, err);
-  }
-  return cudaGetLastError();
+  jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, static_cast<C*>(F1),
+                      rho2, S, beam};
+  if (beam) return launch_row3_kern<T, LG, SWEEP, true>(jb, twc, err, st);
+  return launch_row3_kern<T, LG, SWEEP, false>(jb, twc, err, st);
 }
 
 template <typename T, int LG>

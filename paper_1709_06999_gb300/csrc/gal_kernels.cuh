@@ -205,6 +205,7 @@ __global__ void sweep_kernel(const T* __restrict__ I, SweepT<T> p, int N, T* __r
 template <typename T>
 __global__ void beam_table_kernel(T* __restrict__ tab, int N, double dxy, double c, double bx,
                                   double by) {
+  grid_dep_launch();  // the row pass may start its image copies meanwhile
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 2 * N) return;
   const int n = q < N ? q : q - N;
@@ -366,7 +367,10 @@ template <int THREADS> constexpr int min_blocks_128regs() {
   return THREADS >= 512 ? 1 : 512 / THREADS;
 }
 
-template <typename T, int LG, bool TMA, bool SWEEP, int K>
+// BEAM: multiply the pixels by the primary-beam tables; the kernel is then
+// launched as a programmatic dependent of beam_table_kernel and waits for it
+// only before the first table read (its image copies are already in flight).
+template <typename T, int LG, bool TMA, bool SWEEP, int K, bool BEAM = false>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads,
                                   min_blocks_128regs<Shape3<T, (1 << LG), (2 << LG)>::threads>())
 row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
@@ -380,7 +384,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
   C* __restrict__ F1 = jb.F1;
   const double* __restrict__ rho2 = jb.rho2;
   const double S = jb.S;
-  const T* __restrict__ beam = jb.beam;
+  const T* __restrict__ beam = BEAM ? jb.beam : nullptr;
   constexpr int M = 1 << LG, N = 2 * M;
   using SH = Shape3<T, M, N>;
   using P = typename SH::P;
@@ -456,6 +460,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       issue(0);
       issue(1);
     }
+    if constexpr (BEAM) grid_dep_wait();  // the beam tables
     for (int it = 0;; ++it) {
       const int grp = blockIdx.x + it * gridDim.x;
       if (grp >= ngroups) break;
@@ -473,7 +478,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       C v[V];
 #pragma unroll
       for (int r = 0; r < V; ++r) v[r] = slot[t + r * TT];
-      if (beam) {
+      if constexpr (BEAM) {
 #pragma unroll
         for (int r = 0; r < V; ++r) v[r] = beam_pair(v[r], beam, N, grp * G + g, t + r * TT);
       }
@@ -488,6 +493,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
     C* B = base + (size_t)(G + g) * RS;
     const int row = blockIdx.x * G + g;
     const int irow = (row + M) & (N - 1);
+    if constexpr (BEAM) grid_dep_wait();  // the beam tables
     C v[V];
 #pragma unroll
     for (int r = 0; r < V; ++r) {
@@ -497,7 +503,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
         v[r] = mkc(sweep_pixel(I, sp, N, irow, j), sweep_pixel(I, sp, N, irow, j + 1));
       else
         v[r] = *reinterpret_cast<const C*>(image + (size_t)irow * N + j);
-      if (beam) v[r] = beam_pair(v[r], beam, N, row, n);
+      if constexpr (BEAM) v[r] = beam_pair(v[r], beam, N, row, n);
     }
     transform(v, A, B, row);
   }

@@ -47,6 +47,7 @@ row_c2c_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __restrict
   auto sync = [] { __syncthreads(); };
   const T* __restrict__ beam = jb.beam;
   C* __restrict__ F1 = jb.F1;
+  if (beam) grid_dep_wait();  // launched as a dependent of beam_table_kernel
   for (int r0 = blockIdx.x * G; r0 < N; r0 += gridDim.x * G) {
     const int row = r0 + g;
     const bool act = row < N;
@@ -111,6 +112,9 @@ cudaError_t launch_row_c2c(const RowJob<T>& jb, const void* tw, cudaStream_t st)
   int grid = per_sm * current_device_sms();
   const int need = (N + SH::G - 1) / SH::G;
   if (grid > need) grid = need;
+  if (jb.beam)  // follows beam_table_kernel: start early, wait for the tables in the kernel
+    return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb,
+                            static_cast<const C*>(tw));
   kern<<<grid, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw));
   return cudaGetLastError();
 }
