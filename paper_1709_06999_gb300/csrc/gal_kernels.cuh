@@ -1252,30 +1252,12 @@ __device__ __forceinline__ double block_sum(double x, double* ws) {
 
 // Loop over this thread's uv points, reading the window nodes through G
 // (SMEM: G points into shared memory).
-template <typename T, bool CHI2, bool SMEM, bool EDGE, bool MULTI, bool FULL, typename ACC>
-__device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
-                                              const GatherT<T>& p, const T* __restrict__ u,
-                                              const T* __restrict__ v, const T* __restrict__ re,
-                                              const T* __restrict__ im, const T* __restrict__ w,
-                                              int64_t M, int vec, cplx_t<T>* __restrict__ vis,
-                                              ACC& acc, const MultiPhase<T>* mp) {
-  using C = cplx_t<T>;
-  constexpr int W = Vec16<T>::W;
-  auto point = [&](T uu, T vv) {
-    return sample_point<SMEM, EDGE, MULTI, FULL>(G, win, p, uu, vv, mp);
-  };
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t nq = vec ? M / W : 0;
-  // whole grid-stride rounds, then the R remaining groups in equal contiguous
-  // slices, one per block (coalesced, and no few blocks run a round more
-  // than the rest)
-  const int64_t rounds = nq / gstride;
-  const int64_t rem = nq - rounds * gstride;
-  const int64_t slice = (rem + gridDim.x - 1) / gridDim.x;  // <= blockDim.x
-  const int64_t rem_q = rounds * gstride + (int64_t)blockIdx.x * slice + threadIdx.x;
-  auto group = [&](int64_t q) {  // the W points of group q
-    T uu[W], vv[W], rr[W], ii[W], ww[W];
+// The W points of one group: u, v and (chi-square mode) Re, Im, w.
+template <typename T, bool CHI2> struct PointGroup {
+  T uu[Vec16<T>::W], vv[Vec16<T>::W], rr[Vec16<T>::W], ii[Vec16<T>::W], ww[Vec16<T>::W];
+  __device__ __forceinline__ void load(const T* __restrict__ u, const T* __restrict__ v,
+                                       const T* __restrict__ re, const T* __restrict__ im,
+                                       const T* __restrict__ w, int64_t q) {
     load16(u, q, uu);
     load16(v, q, vv);
     if constexpr (CHI2) {
@@ -1283,6 +1265,48 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
       load16(im, q, ii);
       load16(w, q, ww);
     }
+  }
+};
+
+// Grid-stride layout of the vector groups: whole rounds of gstride groups,
+// then the remainder in equal contiguous slices, one per block (coalesced,
+// and no few blocks run a round more than the rest).
+struct GroupSplit {
+  int64_t nq, gstride, rounds, slice, rem_q;
+  __device__ __forceinline__ GroupSplit(int64_t M, int W, int vec) {
+    nq = vec ? M / W : 0;
+    gstride = (int64_t)gridDim.x * blockDim.x;
+    rounds = nq / gstride;
+    const int64_t rem = nq - rounds * gstride;
+    slice = (rem + gridDim.x - 1) / gridDim.x;  // <= blockDim.x
+    rem_q = rounds * gstride + (int64_t)blockIdx.x * slice + threadIdx.x;
+  }
+  __device__ __forceinline__ bool has_rem() const { return threadIdx.x < slice && rem_q < nq; }
+};
+
+// pre: this thread's first group (its grid index), already loaded by the
+// caller when the grid has at least one whole round; null otherwise.
+template <typename T, bool CHI2, bool SMEM, bool EDGE, bool MULTI, bool FULL, typename ACC>
+__device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, const Window& win,
+                                              const GatherT<T>& p, const T* __restrict__ u,
+                                              const T* __restrict__ v, const T* __restrict__ re,
+                                              const T* __restrict__ im, const T* __restrict__ w,
+                                              int64_t M, int vec, cplx_t<T>* __restrict__ vis,
+                                              ACC& acc, const MultiPhase<T>* mp,
+                                              const PointGroup<T, CHI2>* pre) {
+  using C = cplx_t<T>;
+  constexpr int W = Vec16<T>::W;
+  auto point = [&](T uu, T vv) {
+    return sample_point<SMEM, EDGE, MULTI, FULL>(G, win, p, uu, vv, mp);
+  };
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const GroupSplit sp(M, W, vec);
+  auto compute = [&](const PointGroup<T, CHI2>& g, int64_t q) {  // the W points of group q
+    const T(&uu)[W] = g.uu;
+    const T(&vv)[W] = g.vv;
+    const T(&rr)[W] = g.rr;
+    const T(&ii)[W] = g.ii;
+    const T(&ww)[W] = g.ww;
     C Vs[W];
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -1306,10 +1330,21 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
       for (int e = 0; e < W; ++e) vis[q * W + e] = Vs[e];
     }
   };
+  auto group = [&](int64_t q) {
+    PointGroup<T, CHI2> g;
+    g.load(u, v, re, im, w, q);
+    compute(g, q);
+  };
   int64_t q = gtid;
-  for (int64_t r = 0; r < rounds; ++r, q += gstride) group(q);
-  if (threadIdx.x < slice && rem_q < nq) group(rem_q);
-  for (int64_t k = nq * W + gtid; k < M; k += gstride) {
+  int64_t r = 0;
+  if (pre) {
+    compute(*pre, q);
+    q += sp.gstride;
+    r = 1;
+  }
+  for (; r < sp.rounds; ++r, q += sp.gstride) group(q);
+  if (sp.has_rem()) group(sp.rem_q);
+  for (int64_t k = sp.nq * W + gtid; k < M; k += sp.gstride) {
     const C V = point(u[k], v[k]);
     if constexpr (CHI2) {
       const T dr = re[k] - V.x, di = im[k] - V.y;
@@ -1349,21 +1384,25 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
   const Bounds bd = block_bounds(rho2, p.Sd, p.N);
   const Window win = FULL ? make_window_full(bd, p.N) : make_window(bd, p.N);
   typename Acc<T>::type acc;
-  // the observation does not depend on the column pass: pull this thread's
-  // first group towards L2 while that pass finishes
-  if (vec) {
-    constexpr int W = Vec16<T>::W;
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < M / W) {
-      prefetch_l2(u + q * W);
-      prefetch_l2(v + q * W);
-      if constexpr (CHI2) {
-        prefetch_l2(re + q * W);
-        prefetch_l2(im + q * W);
-        prefetch_l2(w + q * W);
-      }
+  // The observation does not depend on the column pass: while that pass
+  // finishes, load this thread's first group into registers (when the grid
+  // has a whole round) and pull its remainder group, if any, towards L2.
+  constexpr int W = Vec16<T>::W;
+  const GroupSplit gs(M, W, vec);
+  PointGroup<T, CHI2> g0;
+  const bool pre = gs.rounds > 0;  // uniform over the grid
+  if (pre) g0.load(u, v, re, im, w, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (gs.has_rem()) {
+    const int64_t o = gs.rem_q * W;
+    prefetch_l2(u + o);
+    prefetch_l2(v + o);
+    if constexpr (CHI2) {
+      prefetch_l2(re + o);
+      prefetch_l2(im + o);
+      prefetch_l2(w + o);
     }
   }
+  const PointGroup<T, CHI2>* g0p = pre ? &g0 : nullptr;
   grid_dep_wait();  // the window is the column pass's output
   if constexpr (SMEM) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1387,7 +1426,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
         __syncthreads();
       }
       gather_points<T, CHI2, true, EDGE, MULTI, FULL>(sw, win, p, u, v, re, im, w, M, vec, vis, acc,
-                                                      mp);
+                                                      mp, g0p);
     } else {
       // the host sizes the shared window from the same extent, so this is
       // never taken; the result is NaN rather than a read out of bounds
@@ -1402,7 +1441,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
     }
   } else {
     gather_points<T, CHI2, false, EDGE, MULTI, FULL>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc,
-                                                     mp);
+                                                     mp, g0p);
   }
   if constexpr (CHI2) {
     __shared__ double ws[32];
