@@ -269,7 +269,7 @@ int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& s
   const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
   const double S = (double)nxy * dxy;
   GAL_TRY(stage(ctx, 1, st, [&] {
-    if (full) return gal::Plane<T>::rows(image, I, sp, nxy, tw, ctx->F1, rho2, S, beam, st);
+    if (full) return gal::Plane<T>::rows(image, I, sp, nxy, tw, ctx->F1, rho2, S, beam, ctx->err, st);
     return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, beam, st);
   }));
   GAL_TRY(stage(ctx, 2, st, [&] {

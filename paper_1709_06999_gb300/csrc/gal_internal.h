@@ -78,9 +78,10 @@ template <typename T> struct Launch {
 // pass runs with full = true.
 template <typename T> struct Plane {
   static bool supported(int N);  // transform lengths of the full-plane row pass
+  // err: bit 2 is set if a staged copy's wait timed out (never expected)
   static cudaError_t rows(const T* image, const T* I, const SweepParams& sp, int N,
                           const void* tw, void* F1, const double* rho2, double S, const T* beam,
-                          cudaStream_t st);
+                          int* err, cudaStream_t st);
   static int gather_blocks_per_sm(bool chi2, size_t window_smem);
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,

@@ -114,6 +114,28 @@ def test_full_plane_pruned_chi2_and_vis(ctx, dt, PA):
     assert normwise(got, ref_vis) <= TOL_VIS[dt]
 
 
+@pytest.mark.parametrize("beam", [False, True], ids=["no_beam", "beam"])
+def test_full_plane_unaligned_image(ctx, beam):
+    """A float32 image 8- but not 16-byte aligned takes the full-plane row pass
+    that loads pixels directly instead of staging rows with bulk copies."""
+    s = synth()
+    dt = torch.float32
+    p = s.small_image_problem(nxy=256, M=15013, seed=39)
+    kw = dict(pb_fwhm=0.5 * 256 * p.dxy) if beam else {}
+    ref = O.sample_image(rounded(p.image, dt), p.dxy, rounded(p.u, dt), rounded(p.v, dt), p.dRA,
+                         p.dDec, 0.8, full_plane=True, **kw)
+    img = dev(p.image, dt)
+    store = torch.empty(img.numel() + 2, dtype=dt, device="cuda")
+    shifted = store[2:].view(img.shape)  # 8-byte offset from the 256-byte aligned allocation
+    shifted.copy_(img)
+    u_d, v_d = dev(p.u, dt), dev(p.v, dt)
+    a = as_complex(ctx.sample_image(img, p.dxy, u_d, v_d, p.dRA, p.dDec, 0.8, full_plane=True, **kw))
+    b = as_complex(ctx.sample_image(shifted, p.dxy, u_d, v_d, p.dRA, p.dDec, 0.8, full_plane=True,
+                                    **kw))
+    assert normwise(a, ref) <= TOL_VIS[dt]
+    assert normwise(b, ref) <= TOL_VIS[dt]
+
+
 @pytest.mark.parametrize("dt", DTYPES, ids=IDS)
 def test_full_plane_agrees_with_half_plane(ctx, dt):
     """The paper's C2C versus R2C check, on the GPU: two independent spectrum
