@@ -249,6 +249,22 @@ int gal_chi2_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, 
                             const gal_opts* opts, const gal_data* data, double* chi2_out,
                             void* stream);
 
+/* Pipelined host-buffer chi2Image, for a caller that streams model images from
+ * the host (Sect. 4: host-device transfers dominate the paper's GPU timings).
+ * The image is copied into one of two context staging buffers on a context-
+ * owned copy stream, so the copy overlaps the compute of the previous call;
+ * the compute runs on `stream` once its copy is done, and the result is
+ * copied to *chi2_host (ideally pinned) on `stream`.  Nothing is synchronised:
+ * *chi2_host is written, and `image_host` (ideally pinned) may be modified or
+ * freed, only once `stream` has passed this call's work (e.g. after
+ * cudaStreamSynchronize).  Results equal gal_chi2_image_host's bitwise. */
+int gal_chi2_image_host_async_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,
+                                  double dRA, double dDec, double PA, const gal_data* data,
+                                  double* chi2_host, void* stream);
+int gal_chi2_image_host_async_f64(gal_ctx* ctx, const double* image_host, int nxy, double dxy,
+                                  double dRA, double dDec, double PA, const gal_data* data,
+                                  double* chi2_host, void* stream);
+
 /* ---- multi-source composition --------------------------------------------------------- */
 
 /* Largest number of copies in one multi-source call. */

@@ -37,6 +37,7 @@ for _p in ("f32", "f64"):
         f"gal_chi2_image_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
         f"gal_chi2_profile_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, P, P, P]),
         f"gal_chi2_image_host_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
+        f"gal_chi2_image_host_async_{_p}": (I32, [P, P, I32, D, D, D, D, P, P, P]),
         f"gal_get_image_size_{_p}": (I32, [P, P, P, I64, D, D, D, ct.POINTER(I64),
                                             ct.POINTER(D), P]),
         f"gal_sample_image_multi_{_p}": (I32, [P, P, I32, D, D, I32, P, P, P, I64, P, P, P, P]),

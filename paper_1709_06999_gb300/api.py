@@ -322,6 +322,24 @@ class Context:
                    getattr(self.lib, f"gal_chi2_profile_ex_{sfx}")(*head, opts, *tail))
         return out
 
+    def chi2_image_host_async(self, image_host, dxy: float, obs: Observation, out, index: int = 0,
+                              dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0):
+        """Enqueue chi2Image of a host image (pinned) without waiting: its copy
+        overlaps the previous call's compute; the result lands in out[index]
+        (a pinned float64 CPU tensor) once the current stream reaches this call.
+        Neither the image nor out may be touched before then."""
+        if image_host.device.type != "cpu" or out.device.type != "cpu":
+            raise ValueError("image_host and out must be CPU tensors")
+        if out.dtype != torch.float64 or not out.is_contiguous() or not 0 <= index < out.numel():
+            raise ValueError("out must be a contiguous float64 tensor with room for index")
+        if not image_host.is_contiguous():
+            raise ValueError("image_host must be contiguous (it is read after this call returns)")
+        sfx = _suffix(image_host)
+        fn = getattr(self.lib, f"gal_chi2_image_host_async_{sfx}")
+        _check(self.handle, fn(self.handle, image_host.data_ptr(), image_host.shape[0], dxy, dRA,
+                               dDec, PA, obs.handle, out.data_ptr() + 8 * index, self._stream()))
+        return out
+
     def chi2_image_host(self, image_host, dxy: float, obs: Observation, dRA: float = 0.0,
                         dDec: float = 0.0, PA: float = 0.0) -> float:
         """chi2Image from a host (ideally pinned) image; copies in, computes, copies back."""

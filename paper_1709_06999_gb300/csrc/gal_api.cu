@@ -52,6 +52,14 @@ struct gal_ctx {
   size_t stage_img_bytes = 0;
   void* beam = nullptr;         // primary-beam tables of the last call with a beam
   size_t beam_bytes = 0;
+  // pipelined host-buffer calls: two staging images used in turn, a copy
+  // stream, and per-buffer events (copy done, compute done)
+  void* pipe_img[2] = {};
+  size_t pipe_img_bytes[2] = {};
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t pipe_copied[2] = {}, pipe_done[2] = {};
+  double* pipe_chi2 = nullptr;  // device result slots, one per staging image
+  uint64_t pipe_k = 0;          // pipelined calls so far
   void* tw[2][kMaxLog2 + 1] = {};
   int gather_blocks[2][2] = {};  // [f64?][chi2?], global-memory window
   size_t smem_blocks_key[2] = {};  // window bytes the cached count below is for
@@ -570,6 +578,48 @@ int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, do
   return GAL_OK;
 }
 
+// Pipelined host-buffer chi2Image: the image goes into one of two staging
+// buffers on the context's copy stream, so it overlaps the compute of the
+// previous call; the compute waits for its copy, and the next copy into the
+// same buffer waits for that compute.  The result is copied to *chi2_host on
+// `stream`; nothing here synchronises.
+template <typename T>
+int chi2_image_host_async_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, double dRA,
+                            double dDec, double PA, const gal_data* d, double* chi2_host,
+                            void* stream) {
+  if (!ctx || !image_host || !chi2_host || !d) return GAL_E_INVAL;
+  GAL_TRY(check_geometry(nxy, dxy));
+  if (d->device != ctx->device || d->real_bytes != (int)sizeof(T)) return GAL_E_INVAL;
+  if (!aligned(chi2_host, sizeof(double))) return GAL_E_INVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!ctx->copy_stream) {
+    GAL_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+      GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_copied[s], cudaEventDisableTiming));
+      GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_done[s], cudaEventDisableTiming));
+    }
+    GAL_CUDA(ctx, cudaMalloc(&ctx->pipe_chi2, 2 * sizeof(double)));
+  }
+  const int s = (int)(ctx->pipe_k & 1);
+  const size_t bytes = (size_t)nxy * nxy * sizeof(T);
+  if (ctx->pipe_img_bytes[s] < bytes) {  // regrow only once the buffer's last use is done
+    GAL_CUDA(ctx, cudaEventSynchronize(ctx->pipe_done[s]));
+    GAL_CUDA(ctx, grow(&ctx->pipe_img[s], &ctx->pipe_img_bytes[s], bytes));
+  }
+  GAL_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pipe_done[s], 0));
+  GAL_CUDA(ctx, cudaMemcpyAsync(ctx->pipe_img[s], image_host, bytes, cudaMemcpyHostToDevice,
+                                ctx->copy_stream));
+  GAL_CUDA(ctx, cudaEventRecord(ctx->pipe_copied[s], ctx->copy_stream));
+  GAL_CUDA(ctx, cudaStreamWaitEvent(st, ctx->pipe_copied[s], 0));
+  GAL_TRY(chi2_image_t<T>(ctx, static_cast<const T*>(ctx->pipe_img[s]), nxy, dxy, dRA, dDec, PA, d,
+                          ctx->pipe_chi2 + s, stream));
+  GAL_CUDA(ctx, cudaMemcpyAsync(chi2_host, ctx->pipe_chi2 + s, sizeof(double),
+                                cudaMemcpyDeviceToHost, st));
+  GAL_CUDA(ctx, cudaEventRecord(ctx->pipe_done[s], st));
+  ctx->pipe_k++;
+  return GAL_OK;
+}
+
 std::once_flag g_init_once;
 cudaError_t g_init_err = cudaSuccess;
 
@@ -992,8 +1042,13 @@ void gal_destroy(gal_ctx* ctx) {
   cudaDeviceSynchronize();
   for (void* p : {ctx->F1, ctx->Gw, (void*)ctx->partials, (void*)ctx->counter, (void*)ctx->rho2,
                   (void*)ctx->uvrange, ctx->batch_ws, (void*)ctx->batch_ctr,
-                  (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img, ctx->beam})
+                  (void*)ctx->err, (void*)ctx->chi2_dev, ctx->stage_img, ctx->beam,
+                  ctx->pipe_img[0], ctx->pipe_img[1], (void*)ctx->pipe_chi2})
     if (p) cudaFree(p);
+  for (cudaEvent_t e : {ctx->pipe_copied[0], ctx->pipe_copied[1], ctx->pipe_done[0],
+                        ctx->pipe_done[1]})
+    if (e) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   for (auto& a : ctx->tw)
     for (void* p : a)
       if (p) cudaFree(p);
@@ -1330,6 +1385,19 @@ int gal_chi2_profile_ex_f64(gal_ctx* ctx, const double* I, int nr, double Rmin, 
                             void* stream) {
   return chi2_profile_t<double>(ctx, I, nr, Rmin, dR, nxy, dxy, inc, dRA, dDec, PA, data,
                                 chi2_out, stream, opts);
+}
+
+int gal_chi2_image_host_async_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,
+                                  double dRA, double dDec, double PA, const gal_data* data,
+                                  double* chi2_host, void* stream) {
+  return chi2_image_host_async_t<float>(ctx, image_host, nxy, dxy, dRA, dDec, PA, data, chi2_host,
+                                        stream);
+}
+int gal_chi2_image_host_async_f64(gal_ctx* ctx, const double* image_host, int nxy, double dxy,
+                                  double dRA, double dDec, double PA, const gal_data* data,
+                                  double* chi2_host, void* stream) {
+  return chi2_image_host_async_t<double>(ctx, image_host, nxy, dxy, dRA, dDec, PA, data, chi2_host,
+                                         stream);
 }
 
 int gal_chi2_image_host_f32(gal_ctx* ctx, const float* image_host, int nxy, double dxy,

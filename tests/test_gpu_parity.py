@@ -243,6 +243,32 @@ def test_image_alignment_paths_agree(ctx):
 # edge cases
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("dt", DTYPES, ids=IDS)
+def test_host_async_pipeline_equals_host_calls(ctx, dt):
+    """Pipelined host-buffer calls (copy of call k+1 overlapping the compute of
+    call k, two staging buffers in turn) give bitwise the synchronous
+    host-buffer results, for three host images used in rotation."""
+    s = synth()
+    p = s.small_image_problem(nxy=512, M=20011, seed=41)
+    obs = ctx.register(dev(p.u, dt), dev(p.v, dt), dev(p.noise_re, dt), dev(p.noise_im, dt),
+                       dev(p.w, dt))
+    imgs = [torch.as_tensor(p.image * (1.0 + 0.1 * k), dtype=dt).pin_memory() for k in range(3)]
+    n = 11
+    want = [ctx.chi2_image_host(imgs[k % 3], p.dxy, obs, p.dRA, p.dDec, 0.2 * k) for k in range(n)]
+    out = torch.full((n,), float("nan"), dtype=torch.float64).pin_memory()
+    for k in range(n):
+        ctx.chi2_image_host_async(imgs[k % 3], p.dxy, obs, out, k, p.dRA, p.dDec, 0.2 * k)
+    torch.cuda.current_stream().synchronize()
+    assert out.tolist() == want
+    # a larger image regrows the staging buffers after their last use
+    big = torch.as_tensor(np.pad(p.image, 256), dtype=dt).pin_memory()
+    ref = ctx.chi2_image_host(big, p.dxy, obs, p.dRA, p.dDec, 0.3)
+    ctx.chi2_image_host_async(big, p.dxy, obs, out, 0, p.dRA, p.dDec, 0.3)
+    ctx.chi2_image_host_async(imgs[0], p.dxy, obs, out, 1, p.dRA, p.dDec, 0.0)
+    torch.cuda.current_stream().synchronize()
+    assert out[0].item() == ref and out[1].item() == want[0]
+
+
+@pytest.mark.parametrize("dt", DTYPES, ids=IDS)
 def test_empty_observation(ctx, dt):
     e = torch.empty(0, dtype=dt, device="cuda")
     obs = ctx.register(e, e, e, e, e)
