@@ -43,7 +43,7 @@ STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
 KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1, 0>", 2: "col_fft3_kernel<float, 12, 1>",
            3: "gather_kernel<float, 1, 1, 0, 1, 0, 0>"}
 # the full-plane (complex-to-complex) spectrum path
-KERNELS_FULL = {1: "row_c2c_kernel<float, 12, 0>", 2: "col_fft3_kernel<float, 12, 1>",
+KERNELS_FULL = {1: "row_c2c_tma_kernel<float, 12>", 2: "col_fft3_kernel<float, 12, 1>",
                 3: "gather_kernel<float, 1, 1, 0, 1, 0, 1>"}
 # primary beam of a 12 m antenna at 100 GHz: FWHM = K lambda / D, K = 1.13
 PB_FWHM = 1.13 * (299792458.0 / 100e9) / 12.0
@@ -106,9 +106,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(kernel: str, full: bool = False):
     """DRAM bytes per launch from the committed ncu summary, if the kernels
-    have not changed since it was taken."""
+    have not changed since it was taken (full: the full-plane variant's
+    captures, whose column pass keeps more columns under the same name)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -117,7 +118,7 @@ def measured_traffic(kernel: str):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    k = rec.get("kernels", {}).get(kernel)
+    k = rec.get("kernels_full_plane" if full else "kernels", {}).get(kernel)
     return None if k is None else k.get("dram_bytes_per_launch")
 
 
@@ -644,7 +645,7 @@ def run_gpu(args):
     alg = algorithmic_bytes(dom, NXY, M_UV, Kc, nrw, beam="pb_fwhm" in opts)
     achieved = alg / (avg[dom] * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = measured_traffic(kernels[dom])
+    traffic = measured_traffic(kernels[dom], full)
 
     base = None
     if world == 1 and args.cpu_evals > 0:

@@ -1357,11 +1357,16 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 
 // block shape: 512-thread blocks, two per SM, when the window is staged in
 // shared memory (each block its own copy, so one block's window copy and
-// final reduction overlap the other's stream), 256-thread blocks otherwise
-template <bool SMEM> constexpr int gather_threads() { return SMEM ? 512 : 256; }
+// final reduction overlap the other's stream), 256-thread blocks otherwise.
+// The full-plane window is about twice as large, so only one copy fits per
+// SM: one 1024-thread block then keeps the same 32 warps resident.
+template <bool SMEM, bool FULL = false> constexpr int gather_threads() {
+  return SMEM ? (FULL ? 1024 : 512) : 256;
+}
+template <bool SMEM, bool FULL> constexpr int gather_min_blocks() { return SMEM ? (FULL ? 1 : 2) : 3; }
 
 template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false, bool FULL = false>
-__global__ void __launch_bounds__(gather_threads<SMEM>(), SMEM ? 2 : 3)
+__global__ void __launch_bounds__(gather_threads<SMEM, FULL>(), gather_min_blocks<SMEM, FULL>())
 gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes,
               const __grid_constant__ MultiArg<T, MULTI> multi) {
   using C = cplx_t<T>;

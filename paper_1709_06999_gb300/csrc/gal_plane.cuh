@@ -292,11 +292,13 @@ template <typename T> int Plane<T>::gather_blocks_per_sm(bool chi2, size_t windo
     if (chi2) {
       constexpr auto kern = gather_kernel<T, true, true, true, 1, false, true>;
       if (ensure_smem_attr<kern>(window_smem) == cudaSuccess)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true>(), window_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true, true>(),
+                                                      window_smem);
     } else {
       constexpr auto kern = gather_kernel<T, false, true, true, 1, false, true>;
       if (ensure_smem_attr<kern>(window_smem) == cudaSuccess)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true>(), window_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, gather_threads<true, true>(),
+                                                      window_smem);
     }
   } else {
     if (chi2)
@@ -321,7 +323,7 @@ cudaError_t Plane<T>::gather(const void* Gw, const GatherParams& gp, const doubl
   int vec = al16(u) && al16(v);
   if (chi2) vec = vec && al16(re) && al16(im) && al16(w);
   const int nodes = (int)(window_smem / sizeof(C));
-  const int threads = window_smem ? gather_threads<true>() : gather_threads<false>();
+  const int threads = window_smem ? gather_threads<true, true>() : gather_threads<false, true>();
   int grid = blocks;
   if (!chi2) {
     int64_t need = (M + threads - 1) / threads;
