@@ -292,9 +292,10 @@ def _timed(torch, fn, reps, flush=None):
 
 def _single(ctx, r, out=None):
     if r.image is not None:
-        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, out=out)
+        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, out=out,
+                              pb_fwhm=r.pb_fwhm)
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
-                            r.PA, out=out)
+                            r.PA, out=out, pb_fwhm=r.pb_fwhm)
 
 
 def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=200):
@@ -354,6 +355,17 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
                            PA=ch.PA))
     sets["cube"] = (r32, r64, "128 Keplerian-disc channels, nxy U{512,1024,2048}, "
                               "M_c U[1e5,2e6] (ALMA-like layout x channel frequency)")
+    # the same channels, each through its own primary beam: FWHM 1.13 lambda_c / 12 m
+    # (channel frequency: line at 100 GHz, channels 0.5 km/s apart, as in the cube)
+    b32, b64 = [], []
+    for k, (a, b) in enumerate(zip(r32, r64)):
+        v_chan = (k - (len(r32) - 1) / 2) * 0.5
+        theta = 1.13 * (299792458.0 / (100e9 * (1.0 - v_chan / 299792.458))) / 12.0
+        for src, dst in ((a, b32), (b, b64)):
+            dst.append(Request(src.obs, image=src.image, dxy=src.dxy, dRA=src.dRA,
+                               dDec=src.dDec, PA=src.PA, pb_fwhm=theta))
+    sets["cube_beams"] = (b32, b64, "the same 128 channels, each with its primary beam "
+                                    "(FWHM 1.13 lambda_c / 12 m, applied in the row FFT)")
     q = synth.profile_problem(nxy=1024, M=1_000_000, nr=8192, seed=1)
     t32 = [d32(a) for a in (q.u, q.v, q.noise_re, q.noise_im, q.w)]
     o32 = ctx.register(*t32)

@@ -318,6 +318,8 @@ typedef struct gal_request {
   int nxy;
   double dxy, dRA, dDec, PA;
   const gal_data* data;
+  double pb_fwhm;         /* primary-beam FWHM (radians), 0 = none: as gal_opts.pb_fwhm, e.g.
+                             one beam per spectral channel of a cube */
 } gal_request;
 
 /* chi2_out[i] (device, n doubles) = the chi-square of request i: the many

@@ -57,7 +57,7 @@ class Request:
 
     def __init__(self, obs: "Observation", *, image=None, intensity=None, dxy: float,
                  nxy: int | None = None, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
-                 Rmin: float = 0.0, dR: float = 0.0, inc: float = 0.0):
+                 Rmin: float = 0.0, dR: float = 0.0, inc: float = 0.0, pb_fwhm: float = 0.0):
         if (image is None) == (intensity is None):
             raise ValueError("give exactly one of image and intensity")
         self.obs, self.image, self.intensity = obs, image, intensity
@@ -69,6 +69,7 @@ class Request:
             raise ValueError("a profile request needs nxy")
         self.nxy, self.dxy, self.dRA, self.dDec, self.PA = int(nxy), dxy, dRA, dDec, PA
         self.Rmin, self.dR, self.inc = Rmin, dR, inc
+        self.pb_fwhm = pb_fwhm
 
     def _struct(self, ctx: "Context"):
         dt = self.obs.dtype
@@ -78,13 +79,14 @@ class Request:
                 raise TypeError("image dtype must match the observation's")
             keep = img
             return _native.GalRequest(img.data_ptr(), None, 0, 0.0, 0.0, 0.0, self.nxy, self.dxy,
-                                      self.dRA, self.dDec, self.PA, self.obs.handle.value), keep
+                                      self.dRA, self.dDec, self.PA, self.obs.handle.value,
+                                      self.pb_fwhm), keep
         I = ctx._dev(self.intensity).contiguous()
         if I.dtype != dt:
             raise TypeError("intensity dtype must match the observation's")
         return _native.GalRequest(None, I.data_ptr(), I.numel(), self.Rmin, self.dR, self.inc,
                                   self.nxy, self.dxy, self.dRA, self.dDec, self.PA,
-                                  self.obs.handle.value), I
+                                  self.obs.handle.value, self.pb_fwhm), I
 
 
 def _request_array(ctx, requests):
@@ -481,12 +483,12 @@ class Server:
         if req.image is not None:
             t = req.image.to(self.device).contiguous()
             st = _native.GalRequest(t.data_ptr(), None, 0, 0.0, 0.0, 0.0, req.nxy, req.dxy,
-                                    req.dRA, req.dDec, req.PA, req.obs.handle.value)
+                                    req.dRA, req.dDec, req.PA, req.obs.handle.value, req.pb_fwhm)
         else:
             t = req.intensity.to(self.device).contiguous()
             st = _native.GalRequest(None, t.data_ptr(), t.numel(), req.Rmin, req.dR, req.inc,
                                     req.nxy, req.dxy, req.dRA, req.dDec, req.PA,
-                                    req.obs.handle.value)
+                                    req.obs.handle.value, req.pb_fwhm)
         if t.dtype != req.obs.dtype:
             raise TypeError("model dtype must match the observation's")
         return st, t

@@ -675,6 +675,7 @@ int check_request(gal_ctx* ctx, const gal_request& r) {
   if (!d || d->device != ctx->device) return GAL_E_INVAL;
   GAL_TRY(check_geometry(r.nxy, r.dxy));
   if (!std::isfinite(r.dRA) || !std::isfinite(r.dDec) || !std::isfinite(r.PA)) return GAL_E_INVAL;
+  if (!(r.pb_fwhm >= 0.0) || !std::isfinite(r.pb_fwhm)) return GAL_E_INVAL;
   const size_t rb = (size_t)d->real_bytes;
   if ((r.image != nullptr) == (r.intensity != nullptr)) return GAL_E_INVAL;
   if (r.image) {
@@ -700,7 +701,7 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
   size_t bytes = 0;
   size_t nctr = 0;
   struct Off {
-    size_t f1, gw, part;
+    size_t f1, gw, part, bm;
   };
   std::vector<Off> offs[2];
   for (int i = 0; i < n; ++i) {
@@ -745,6 +746,12 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
     bytes = round_up(bytes + round_up((size_t)bd.nrw * bd.Kc * cb, 16) + 16, 256);
     o.part = bytes;
     bytes = round_up(bytes + sizeof(double) * (size_t)b.grid, 256);
+    o.bm = 0;
+    if (r.pb_fwhm > 0.0) {  // the request's beam tables: 2N values
+      o.bm = bytes;
+      bytes = round_up(bytes + 2 * (size_t)r.nxy * (size_t)d->real_bytes, 256);
+      b.bp = gal::beam_params(r.pb_fwhm, r.dRA, r.dDec, r.PA);
+    }
     b.counter = reinterpret_cast<unsigned*>(nctr);  // index, resolved below
     ++nctr;
     pl.items[p].push_back(b);
@@ -765,6 +772,7 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
       b.F1 = base + offs[p][k].f1;
       b.Gw = base + offs[p][k].gw;
       b.partials = reinterpret_cast<double*>(base + offs[p][k].part);
+      b.beam = offs[p][k].bm ? base + offs[p][k].bm : nullptr;
       b.counter = ctx->batch_ctr + reinterpret_cast<size_t>(b.counter);
     }
   return GAL_OK;
@@ -791,6 +799,13 @@ int enqueue_items(gal_ctx* ctx, const std::vector<gal::BatchItem>& items,
   const void* const* tw = ctx->tw[prec_index<T>()];
   const int n = (int)items.size();
   int nl = 0;
+  if (std::any_of(items.begin(), items.end(), [](const gal::BatchItem& b) { return b.beam; })) {
+    GAL_TRY(stage(ctx, 1, st, [&] {
+      return gal::BatchLaunch<T>::beams(items.data(), n, &nl, st);
+    }));
+    ctx->launches += nl - 1;
+    nl = 0;
+  }
   GAL_TRY(stage(ctx, 1, st, [&] {
     return gal::BatchLaunch<T>::rows(items.data(), n, tw, ctx->err, sh, &nl, st);
   }));
@@ -817,14 +832,16 @@ int enqueue_rest(gal_ctx* ctx, const gal_request* reqs, const BatchPlan& pl, dou
   for (int i : pl.single) {
     const gal_request& r = reqs[i];
     const gal::SweepParams sp{r.Rmin, r.dR, r.dxy, r.inc, r.nr};
+    CallOpts o;
+    o.pb_fwhm = r.pb_fwhm;
     if (r.data->real_bytes == 8)
       GAL_TRY(chi2_impl<double>(ctx, static_cast<const double*>(r.image),
                                 static_cast<const double*>(r.intensity), sp, r.nxy, r.dxy, r.dRA,
-                                r.dDec, r.PA, r.data, chi2_out + i, st));
+                                r.dDec, r.PA, r.data, chi2_out + i, st, nullptr, o));
     else
       GAL_TRY(chi2_impl<float>(ctx, static_cast<const float*>(r.image),
                                static_cast<const float*>(r.intensity), sp, r.nxy, r.dxy, r.dRA,
-                               r.dDec, r.PA, r.data, chi2_out + i, st));
+                               r.dDec, r.PA, r.data, chi2_out + i, st, nullptr, o));
   }
   return GAL_OK;
 }
@@ -945,7 +962,8 @@ bool same_structure(const std::vector<gal_request>& a, const gal_request* b, int
   if ((int)a.size() != n) return false;
   for (int i = 0; i < n; ++i)
     if (a[i].data != b[i].data || a[i].nxy != b[i].nxy ||
-        (a[i].image == nullptr) != (b[i].image == nullptr))
+        (a[i].image == nullptr) != (b[i].image == nullptr) ||
+        (a[i].pb_fwhm > 0.0) != (b[i].pb_fwhm > 0.0))
       return false;
   return true;
 }

@@ -27,8 +27,9 @@ inline int chunk_of(const BatchShape& sh) {
 }
 
 // rows: the chunk `idx[0..n)` of items, all of length 2^(LG+1), all swept
-// (SWEEP) or all images
-template <typename T, int LG, bool SWEEP>
+// (SWEEP) or all images, all with a beam (BEAM, its tables already computed
+// earlier in the stream) or none
+template <typename T, int LG, bool SWEEP, bool BEAM>
 cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int* err,
                  const BatchShape& sh, cudaStream_t st) {
   using C = cplx_t<T>;
@@ -39,11 +40,11 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
     const BatchItem& b = it[idx[k]];
     jb.j[k] = RowJob<T>{static_cast<const T*>(b.image), static_cast<const T*>(b.I),
                         SWEEP ? sweep_cast<T>(b.sp) : SweepT<T>{}, static_cast<C*>(b.F1), b.rho2,
-                        b.S, /*beam=*/nullptr};
+                        b.S, BEAM ? static_cast<const T*>(b.beam) : nullptr};
   }
   const C* twc = static_cast<const C*>(tw);
   if constexpr (!SWEEP) {
-    constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs>;
+    constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs, BEAM>;
     const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
     cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
@@ -58,7 +59,7 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
     if (x < 1) x = 1;
     kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, twc, err);
   } else {
-    constexpr auto kern = row_fft3_kernel<T, LG, false, true, kBatchJobs>;
+    constexpr auto kern = row_fft3_kernel<T, LG, false, true, kBatchJobs, BEAM>;
     const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
     const cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
@@ -160,10 +161,30 @@ cudaError_t for_chunks(const BatchItem* it, int n, const BatchShape& sh, Pick&& 
 }  // namespace batch
 
 template <typename T>
+cudaError_t BatchLaunch<T>::beams(const BatchItem* it, int n, int* launches, cudaStream_t st) {
+  const BatchShape sh{1, kBatchJobs};
+  auto pick = [](const BatchItem& b) { return b.beam != nullptr; };
+  auto key = [](const BatchItem&) { return 0; };
+  return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem&) {
+    Jobs<BeamJob<T>, kBatchJobs> jb{};
+    int nmax = 1;
+    for (int k = 0; k < m; ++k) {
+      const BatchItem& b = it[idx[k]];
+      jb.j[k] = BeamJob<T>{static_cast<T*>(b.beam), b.N, b.sp.dxy, b.bp.c, b.bp.bx, b.bp.by};
+      nmax = b.N > nmax ? b.N : nmax;
+    }
+    beam_tables_kernel<T, kBatchJobs><<<dim3((2 * nmax + 255) / 256, m), 256, 0, st>>>(jb);
+    const cudaError_t e = cudaGetLastError();
+    if (!e) ++*launches;
+    return e;
+  });
+}
+
+template <typename T>
 cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* tw, int* err,
                                  const BatchShape& sh, int* launches, cudaStream_t st) {
   auto pick = [](const BatchItem&) { return true; };
-  auto key = [](const BatchItem& b) { return b.N * 2 + (b.I ? 1 : 0); };
+  auto key = [](const BatchItem& b) { return b.N * 4 + (b.beam ? 2 : 0) + (b.I ? 1 : 0); };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
     const int lg = ilog2i(b0.N);
     const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg - 1, [&](auto L) {
@@ -171,8 +192,11 @@ cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* 
       if constexpr (LG > 12) {
         return cudaErrorNotSupported;
       } else {
-        return b0.I ? batch::rows<T, LG, true>(it, idx, m, tw[lg], err, sh, st)
-                    : batch::rows<T, LG, false>(it, idx, m, tw[lg], err, sh, st);
+        if (b0.beam)
+          return b0.I ? batch::rows<T, LG, true, true>(it, idx, m, tw[lg], err, sh, st)
+                      : batch::rows<T, LG, false, true>(it, idx, m, tw[lg], err, sh, st);
+        return b0.I ? batch::rows<T, LG, true, false>(it, idx, m, tw[lg], err, sh, st)
+                    : batch::rows<T, LG, false, false>(it, idx, m, tw[lg], err, sh, st);
       }
     });
     if (!e) ++*launches;

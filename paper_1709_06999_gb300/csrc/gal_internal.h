@@ -5,7 +5,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace gal {
+
+// Parameters of the primary-beam tables (Sect. 2.1): c = 4 ln 2 / fwhm^2 and
+// the beam centre (bx, by) = R (dRA, dDec) on the image grid, R the matrix of
+// the Sect. 3.2 rotation (see beam_table_kernel).  One host function serves
+// single calls and batches, so their tables are identical.
+struct BeamParams {
+  double c, bx, by;
+};
+inline BeamParams beam_params(double fwhm, double dRA, double dDec, double PA) {
+  const double cp = std::cos(PA), sp = std::sin(PA);
+  return BeamParams{4.0 * std::log(2.0) / (fwhm * fwhm), dRA * cp - dDec * sp, dRA * sp + dDec * cp};
+}
 
 // profile -> image parameters (all radians; Sect. 2 sampleProfile)
 struct SweepParams {
@@ -115,6 +129,8 @@ struct BatchItem {
   size_t wbytes;       // window bytes staged in shared memory (0: read from L2)
   bool edge;           // window reaches the edge of the half spectrum
   int grid;            // gather blocks (those of a single call of this request)
+  void* beam;          // workspace: the request's 2N beam factors (null: no beam)
+  BeamParams bp;       // their parameters
 };
 
 // Launch shape of the batched passes.  Results do not depend on it (every
@@ -130,6 +146,8 @@ struct BatchShape {
 // length 2^lg.  `launches` is incremented per kernel launched.
 template <typename T> struct BatchLaunch {
   static bool supported(int N);  // lengths the batched passes cover
+  // the beam tables of the items that have a beam (launches only if some do)
+  static cudaError_t beams(const BatchItem* items, int n, int* launches, cudaStream_t st);
   static cudaError_t rows(const BatchItem* items, int n, const void* const* tw, int* err,
                           const BatchShape& shape, int* launches, cudaStream_t st);
   static cudaError_t cols(const BatchItem* items, int n, const void* const* tw,

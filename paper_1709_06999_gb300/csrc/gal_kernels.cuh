@@ -203,15 +203,32 @@ __global__ void sweep_kernel(const T* __restrict__ I, SweepT<T> p, int N, T* __r
 // column term of shifted column n (image column (n + N/2) mod N), entry N + n
 // the row term of shifted row n; both in FP64, rounded once to T.
 template <typename T>
+__device__ __forceinline__ T beam_entry(int q, int N, double dxy, double c, double bx, double by) {
+  const int n = q < N ? q : q - N;
+  const int j = (n + N / 2) & (N - 1);
+  const double s = (double)(N / 2 - j) * dxy + (q < N ? bx : by);
+  return (T)exp(-c * s * s);
+}
+
+template <typename T>
 __global__ void beam_table_kernel(T* __restrict__ tab, int N, double dxy, double c, double bx,
                                   double by) {
   grid_dep_launch();  // the row pass may start its image copies meanwhile
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 2 * N) return;
-  const int n = q < N ? q : q - N;
-  const int j = (n + N / 2) & (N - 1);
-  const double s = (double)(N / 2 - j) * dxy + (q < N ? bx : by);
-  tab[q] = (T)exp(-c * s * s);
+  if (q < 2 * N) tab[q] = beam_entry<T>(q, N, dxy, c, bx, by);
+}
+
+// the tables of up to K requests of a batch, grid row y = request y
+template <typename T> struct BeamJob {
+  T* tab;
+  int N;
+  double dxy, c, bx, by;
+};
+template <typename T, int K>
+__global__ void beam_tables_kernel(const __grid_constant__ Jobs<BeamJob<T>, K> jobs) {
+  const BeamJob<T>& jb = jobs.j[blockIdx.y];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * jb.N; q += gridDim.x * blockDim.x)
+    jb.tab[q] = beam_entry<T>(q, jb.N, jb.dxy, jb.c, jb.bx, jb.by);
 }
 
 // Primary-beam factor (Sect. 2.1: the visibility is the transform of A I).
@@ -1658,10 +1675,8 @@ cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& s
 template <typename T>
 cudaError_t Launch<T>::beam_table(T* tab, int N, double dxy, double fwhm, double dRA, double dDec,
                                   double PA, cudaStream_t st) {
-  const double c = 4.0 * std::log(2.0) / (fwhm * fwhm);
-  const double cp = std::cos(PA), sp = std::sin(PA);
-  const double bx = dRA * cp - dDec * sp, by = dRA * sp + dDec * cp;  // R (dRA, dDec)
-  beam_table_kernel<T><<<(2 * N + 255) / 256, 256, 0, st>>>(tab, N, dxy, c, bx, by);
+  const BeamParams b = beam_params(fwhm, dRA, dDec, PA);
+  beam_table_kernel<T><<<(2 * N + 255) / 256, 256, 0, st>>>(tab, N, dxy, b.c, b.bx, b.by);
   return cudaGetLastError();
 }
 

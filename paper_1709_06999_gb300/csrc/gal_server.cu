@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -55,7 +56,8 @@ int pow2_side(int n) { return n >= 4 && n <= 8192 && (n & (n - 1)) == 0; }
 // (three half spectra); a batch needs less per request
 size_t need_bytes(const gal_request& r, int real_bytes) {
   const size_t spec = (size_t)r.nxy * (size_t)(r.nxy / 2 + 1) * 2 * (size_t)real_bytes;
-  return 3 * spec;
+  const size_t beam = r.pb_fwhm > 0.0 ? 2 * (size_t)r.nxy * (size_t)real_bytes : 0;
+  return 3 * spec + beam;
 }
 
 }  // namespace
@@ -131,18 +133,19 @@ int gal_server::launch(Slot& s, std::vector<Pending>& grp) {
   int st;
   if (n == 1) {
     const gal_request& r = grp[0].req;
+    const gal_opts o{r.pb_fwhm, 0};  // a request's only option: its primary beam
     if (grp[0].prec == 0) {
-      st = r.image ? gal_chi2_image_f32(s.ctx, static_cast<const float*>(r.image), r.nxy, r.dxy,
-                                        r.dRA, r.dDec, r.PA, r.data, s.d_out, s.st)
-                   : gal_chi2_profile_f32(s.ctx, static_cast<const float*>(r.intensity), r.nr,
-                                          r.Rmin, r.dR, r.nxy, r.dxy, r.inc, r.dRA, r.dDec, r.PA,
-                                          r.data, s.d_out, s.st);
+      st = r.image ? gal_chi2_image_ex_f32(s.ctx, static_cast<const float*>(r.image), r.nxy,
+                                           r.dxy, r.dRA, r.dDec, r.PA, &o, r.data, s.d_out, s.st)
+                   : gal_chi2_profile_ex_f32(s.ctx, static_cast<const float*>(r.intensity), r.nr,
+                                             r.Rmin, r.dR, r.nxy, r.dxy, r.inc, r.dRA, r.dDec,
+                                             r.PA, &o, r.data, s.d_out, s.st);
     } else {
-      st = r.image ? gal_chi2_image_f64(s.ctx, static_cast<const double*>(r.image), r.nxy,
-                                        r.dxy, r.dRA, r.dDec, r.PA, r.data, s.d_out, s.st)
-                   : gal_chi2_profile_f64(s.ctx, static_cast<const double*>(r.intensity), r.nr,
-                                          r.Rmin, r.dR, r.nxy, r.dxy, r.inc, r.dRA, r.dDec, r.PA,
-                                          r.data, s.d_out, s.st);
+      st = r.image ? gal_chi2_image_ex_f64(s.ctx, static_cast<const double*>(r.image), r.nxy,
+                                           r.dxy, r.dRA, r.dDec, r.PA, &o, r.data, s.d_out, s.st)
+                   : gal_chi2_profile_ex_f64(s.ctx, static_cast<const double*>(r.intensity), r.nr,
+                                             r.Rmin, r.dR, r.nxy, r.dxy, r.inc, r.dRA, r.dDec,
+                                             r.PA, &o, r.data, s.d_out, s.st);
     }
   } else {
     std::vector<gal_request> rq(n);
@@ -328,6 +331,7 @@ static int make_pending(const gal_request* req, Pending* p) {
   if (gal_data_info(req->data, &M, &rb) != GAL_OK) return GAL_E_INVAL;
   if ((req->image != nullptr) == (req->intensity != nullptr)) return GAL_E_INVAL;
   if (!pow2_side(req->nxy) || !(req->dxy > 0.0)) return GAL_E_INVAL;
+  if (!(req->pb_fwhm >= 0.0) || !std::isfinite(req->pb_fwhm)) return GAL_E_INVAL;
   p->req = *req;
   p->prec = rb == 8 ? 1 : 0;
   p->need = need_bytes(*req, rb);

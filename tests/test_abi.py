@@ -72,3 +72,33 @@ def test_options_struct_layout():
     text = open(HEADER).read()
     assert re.search(r"typedef struct gal_opts \{\s*double pb_fwhm;\s*int full_plane;\s*\} gal_opts;",
                      text)
+
+
+def test_struct_layouts_match_c(tmp_path):
+    """sizeof and field offsets of the header's structs, compiled by the C
+    compiler, equal those of the binding's ctypes mirrors."""
+    import ctypes as ct
+    import shutil
+    from paper_1709_06999_gb300 import _native
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"gal_opts": _native.GalOpts, "gal_request": _native.GalRequest,
+               "gal_server_stats": _native.GalServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "galario_gb300.h"',
+             'int main(void) {']
+    for name, cls in mirrors.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in mirrors.items():
+        assert int(got[name]) == ct.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)

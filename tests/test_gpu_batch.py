@@ -29,9 +29,21 @@ def make_obs(ctx, u, v, w, nre, nim, dt):
 
 def single(ctx, r: Request):
     if r.image is not None:
-        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA)
+        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, pb_fwhm=r.pb_fwhm)
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
-                            r.PA)
+                            r.PA, pb_fwhm=r.pb_fwhm)
+
+
+def with_beams(reqs):
+    """The same requests with a primary beam on two of every three, its width
+    varying from request to request like a cube's channels (FWHM ~ lambda)."""
+    out = []
+    for k, r in enumerate(reqs):
+        pb = 0.0 if k % 3 == 2 else (0.3 + 0.04 * k) * r.nxy * r.dxy
+        out.append(Request(r.obs, image=r.image, intensity=r.intensity, nxy=r.nxy, dxy=r.dxy,
+                           dRA=r.dRA, dDec=r.dDec, PA=r.PA, Rmin=r.Rmin, dR=r.dR, inc=r.inc,
+                           pb_fwhm=pb))
+    return out
 
 
 def mixed_requests(ctx, dt, seed=0, n_img=10, n_prof=6):
@@ -195,3 +207,83 @@ def test_cube_channels_at_their_sizes_match_oracle():
         ref = oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w, r.dRA,
                                 r.dDec, r.PA)
         assert abs(g - ref) <= TOL_CHI2[dt] * abs(ref), (r.nxy, g, ref)
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_batch_with_beams_equals_single_calls_bitwise(dt):
+    """Per-request primary beams (images and profiles, with and without a
+    beam in one batch): bitwise the single calls with the same beam."""
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, dt, seed=13, n_img=8, n_prof=5)
+    reqs = with_beams(reqs)
+    got = ctx.chi2_batch(reqs)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    assert torch.equal(got, want), (got - want).abs().max().item()
+    plain = ctx.chi2_batch([Request(r.obs, image=r.image, intensity=r.intensity, nxy=r.nxy,
+                                    dxy=r.dxy, dRA=r.dRA, dDec=r.dDec, PA=r.PA, Rmin=r.Rmin,
+                                    dR=r.dR, inc=r.inc) for r in reqs])
+    # without a beam the result is the plain batch's; with one it differs for the
+    # cube channels (about 1 Jy each; the test profiles are ~1e-14 Jy per pixel,
+    # far below the unit noise, so no factor can move their chi-square)
+    for k, r in enumerate(reqs):
+        if r.pb_fwhm == 0.0:
+            assert got[k].item() == plain[k].item(), k
+        elif r.image is not None:
+            assert got[k].item() != plain[k].item(), k
+
+
+def test_batch_with_beams_matches_oracle():
+    ctx = Context(0)
+    dt = torch.float32
+    reqs, keep = mixed_requests(ctx, dt, seed=15, n_img=3, n_prof=2)
+    reqs = with_beams(reqs)
+    got = ctx.chi2_batch(reqs).cpu().numpy()
+    for r, g in zip(reqs, got):
+        u, v, re, im, w = (t.double().cpu().numpy() for t in r.obs._tensors)
+        if r.image is not None:
+            ref = oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w,
+                                    r.dRA, r.dDec, r.PA, pb_fwhm=r.pb_fwhm)
+        else:
+            ref = oracle.chi2_profile(r.intensity.double().cpu().numpy(), r.Rmin, r.dR, r.nxy,
+                                      r.dxy, u, v, re, im, w, r.dRA, r.dDec, r.PA, r.inc,
+                                      pb_fwhm=r.pb_fwhm)
+        assert abs(g - ref) <= TOL_CHI2[dt] * abs(ref), (g, ref, r.pb_fwhm)
+
+
+def test_graph_with_beams_replay_and_update():
+    """A captured batch with beams replays to the single calls' results; new
+    offsets and position angles (which move each beam's centre on the grid)
+    update it in place; adding or removing a beam changes its structure."""
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=17, n_img=5, n_prof=3)
+    reqs = with_beams(reqs)
+    g = ctx.capture_batch(reqs)
+    out = g.launch().clone()
+    assert torch.equal(out, torch.stack([single(ctx, r) for r in reqs]))
+    new = [Request(r.obs, image=r.image, intensity=r.intensity, nxy=r.nxy, dxy=r.dxy,
+                   dRA=r.dRA + 2e-7, dDec=r.dDec - 1e-7, PA=r.PA + 0.4, Rmin=r.Rmin, dR=r.dR,
+                   inc=r.inc, pb_fwhm=r.pb_fwhm * 1.1) for r in reqs]
+    g.update(new)
+    out = g.launch().clone()
+    assert torch.equal(out, torch.stack([single(ctx, r) for r in new]))
+    flipped = list(new)
+    k = next(i for i, r in enumerate(new) if r.pb_fwhm == 0.0)
+    r = new[k]
+    flipped[k] = Request(r.obs, image=r.image, intensity=r.intensity, nxy=r.nxy, dxy=r.dxy,
+                         dRA=r.dRA, dDec=r.dDec, PA=r.PA, Rmin=r.Rmin, dR=r.dR, inc=r.inc,
+                         pb_fwhm=0.5 * r.nxy * r.dxy)
+    with pytest.raises(GalError):
+        g.update(flipped)
+    g.close()
+
+
+def test_invalid_beam_in_batch_launches_nothing():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=19, n_img=2, n_prof=1)
+    n0 = ctx.launch_count()
+    r = reqs[0]
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(GalError):
+            ctx.chi2_batch(list(reqs) + [Request(r.obs, image=r.image, intensity=r.intensity,
+                                                 nxy=r.nxy, dxy=r.dxy, pb_fwhm=bad)])
+    assert ctx.launch_count() == n0

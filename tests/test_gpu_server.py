@@ -55,9 +55,9 @@ def requests(data, dt, n, seed=1, sizes=(32, 64, 128, 256, 512)):
 def single(ctx, r):
     obs = ctx.register(*r.obs._tensors)
     if r.image is not None:
-        return ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA).item()
+        return ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA, pb_fwhm=r.pb_fwhm).item()
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, obs, r.inc, r.dRA, r.dDec,
-                            r.PA).item()
+                            r.PA, pb_fwhm=r.pb_fwhm).item()
 
 
 @pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
@@ -78,6 +78,25 @@ def test_alone_equals_mix(dt):
     assert st["completed"] == 2 * len(reqs)
     assert st["launches"] < 2 * len(reqs)            # some requests were batched
     assert st["max_inflight"] > 1                     # and overlapped on the device
+    srv.close()
+
+
+def test_beams_alone_equal_mix():
+    """Requests with per-request primary beams, served alone and in a burst:
+    bitwise equal to each other and to single calls."""
+    dt = torch.float32
+    srv = Server(0, hbm_budget=8 * 10**9, slots=4, max_batch=8)
+    data = datasets(srv, 4, dt, seed=8)
+    reqs = []
+    for k, r in enumerate(requests(data, dt, 24, seed=9)):
+        r.pb_fwhm = 0.0 if k % 4 == 3 else (0.4 + 0.02 * k) * r.nxy * r.dxy
+        reqs.append(r)
+    alone = [srv.wait(srv.submit(r))[0] for r in reqs]
+    tickets = srv.submit_many(reqs)
+    mix = [srv.wait(t)[0] for t in tickets]
+    assert mix == alone
+    ctx = Context(0)
+    assert [single(ctx, r) for r in reqs] == alone
     srv.close()
 
 
@@ -147,6 +166,10 @@ def test_submit_rejects_bad_requests():
     img = dev(np.zeros((48, 48)), torch.float32)               # not a power of two
     with pytest.raises(GalError):
         srv.submit(Request(data[0], image=img, dxy=1e-8))
+    img64 = dev(np.zeros((64, 64)), torch.float32)
+    for bad in (-1.0, float("nan")):                            # a beam must be >= 0, finite
+        with pytest.raises(GalError):
+            srv.submit(Request(data[0], image=img64, dxy=1e-8, pb_fwhm=bad))
     with pytest.raises(GalError):
         srv.wait(123456789)                                   # unknown ticket
     srv.close()
