@@ -335,6 +335,75 @@ def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=2
     return res
 
 
+def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200):
+    """The widened paths at the headline workload: multi-source chi2 (K copies
+    of the model, one FFT, K phase terms per point; L2 flushed before every
+    step, each step event-timed), registration from baselines in metres with
+    one frequency per visibility, and get_image_size on the same coverage (both
+    return to the host, so they are wall-clock timed per call)."""
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(31)
+    arc = math.pi / 648000
+    res = {}
+    for K in (4, 16):
+        dra = [float(x) for x in rng.uniform(-0.5, 0.5, K) * arc]
+        ddec = [float(x) for x in rng.uniform(-0.5, 0.5, K) * arc]
+        amp = [float(x) for x in rng.uniform(0.2, 1.0, K)]
+
+        def step(i):
+            ctx.chi2_image_multi(img, p.dxy, obs, dra, ddec, amp, params[i % len(params)][2],
+                                 out=out)
+        for i in range(3):
+            step(i)
+        ctx.set_stage_timing(True)
+        for i in range(3):
+            flush_l2()
+            step(i)
+        cal = ctx.stage_times()
+        ctx.set_stage_timing(False)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for i in range(steps):
+            flush_l2()
+            ev[i][0].record(stream)
+            step(i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        res[f"multi_source_K{K}"] = {
+            "value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms, "sources": K,
+            "stages_us_per_step": {STAGES[s]: round(1000 * cal[s][0] / 3, 2)
+                                   for s in range(4) if cal[s][1]}}
+    # one frequency per visibility around 100 GHz (the coverage's 93 channels
+    # span +-3.75 %), baselines in metres = u c / nu
+    M = p.u.size
+    nu = 100e9 * (1.0 + rng.uniform(-0.0375, 0.0375, M))
+    d32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    u_m, v_m, nu_d = d32(p.u * 299792458.0 / nu), d32(p.v * 299792458.0 / nu), d32(nu)
+    rest = [t.contiguous() for t in obs._tensors[2:]]
+    ctx.register_freq(u_m, v_m, nu_d, *rest).close()
+    torch.cuda.synchronize(dev)
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.register_freq(u_m, v_m, nu_d, *rest).close()
+    ms_f = 1000.0 * (time.perf_counter() - t0) / reps
+    res["freq_registration"] = {
+        "ms_per_registration": ms_f, "points": M,
+        "note": "u_m, v_m, nu (f32) -> u, v in wavelengths (FP64 product, rounded once), then "
+                "the uv extent and its read-back; includes the handle's allocation"}
+    u_d, v_d = obs._tensors[0], obs._tensors[1]
+    ctx.get_image_size(u_d, v_d)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        nxy, dxy = ctx.get_image_size(u_d, v_d)
+    res["image_size"] = {"ms_per_call": 1000.0 * (time.perf_counter() - t0) / reps, "nxy": nxy,
+                         "dxy_arcsec": dxy / arc, "points": M,
+                         "note": "criterion (iia) of Sect. 3.3 on the 5e6-point coverage"}
+    return res
+
+
 def measure_batched(torch, ctx, dev, flush, reps=3):
     """Spectral cube (128 Keplerian channels, nxy in {512, 1024, 2048}, M_c in
     [1e5, 2e6]) and 64 ring-profile walkers (nxy 1024, M 1e6 shared): one
@@ -694,6 +763,7 @@ def run_gpu(args):
         line["cpu_baseline"] = base
     if world == 1 and not args.no_extras:
         line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out)
+        line["next"] = measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out)
         line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
         line["serving"] = measure_serving(torch, dev)
     print(json.dumps(line), flush=True)
