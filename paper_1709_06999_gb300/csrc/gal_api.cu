@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <initializer_list>
 #include <map>
@@ -115,7 +116,9 @@ int log2i(int n) {
 }
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-uint64_t g_ws_generation = 0;  // every reallocation of any context's workspace
+// every reallocation of any context's workspace (contexts may live on
+// different host threads, e.g. the server's workers)
+std::atomic<uint64_t> g_ws_generation{0};
 
 cudaError_t grow(void** p, size_t* have, size_t need) {
   if (*have >= need) return cudaSuccess;

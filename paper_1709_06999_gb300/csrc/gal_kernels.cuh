@@ -17,6 +17,7 @@
 #include "gal_fft3.cuh"
 #include "gal_tma.cuh"
 
+#include <atomic>
 #include <limits>
 #include <type_traits>
 #include <utility>
@@ -1496,17 +1497,24 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
 // ---------------------------------------------------------------------------
 
 // Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
-// the current device (the attribute is per device; set once per size).
+// the current device (the attribute is per device; set once per size).  The
+// cache is atomic: the server's scheduler thread and callers' threads launch
+// the same kernels on their own contexts.
 template <auto Kern> cudaError_t ensure_smem_attr(size_t smem) {
   constexpr int kDev = 64;
-  static size_t done[kDev] = {};
+  static std::atomic<size_t> done[kDev] = {};
   if (smem <= 48 * 1024) return cudaSuccess;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e) return e;
-  if (dev >= 0 && dev < kDev && done[dev] >= smem) return cudaSuccess;
+  if (dev >= 0 && dev < kDev && done[dev].load(std::memory_order_relaxed) >= smem)
+    return cudaSuccess;
   e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && dev >= 0 && dev < kDev) done[dev] = smem;
+  if (e == cudaSuccess && dev >= 0 && dev < kDev) {
+    size_t have = done[dev].load(std::memory_order_relaxed);
+    while (have < smem && !done[dev].compare_exchange_weak(have, smem)) {
+    }
+  }
   return e;
 }
 
@@ -1535,17 +1543,20 @@ constexpr int kMaxWindowSmem = 200 * 1024;
 
 inline int row_threads_per_row(int N) { return N / 2 >= 8 ? N / 16 : 1; }
 
-// multiprocessor count of the current device (cached per device)
+// multiprocessor count of the current device (cached per device; atomic for
+// the same reason as ensure_smem_attr)
 inline int current_device_sms() {
-  static int cache[64] = {0};
+  static std::atomic<int> cache[64] = {};
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 1;
-  if (!cache[d]) {
+  int c = cache[d].load(std::memory_order_relaxed);
+  if (!c) {
     int n = 0;
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
-    cache[d] = n > 0 ? n : 1;
+    c = n > 0 ? n : 1;
+    cache[d].store(c, std::memory_order_relaxed);
   }
-  return cache[d];
+  return c;
 }
 inline int col_threads_per_col(int N) { return N >= 8 ? N / 8 : 1; }
 
