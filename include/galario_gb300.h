@@ -320,6 +320,7 @@ typedef struct gal_request {
   const gal_data* data;
   double pb_fwhm;         /* primary-beam FWHM (radians), 0 = none: as gal_opts.pb_fwhm, e.g.
                              one beam per spectral channel of a cube */
+  int full_plane;         /* 1 = full-plane spectrum, as gal_opts.full_plane (0 or 1) */
 } gal_request;
 
 /* chi2_out[i] (device, n doubles) = the chi-square of request i: the many

@@ -53,7 +53,7 @@ class GalRequest(ct.Structure):
     """struct gal_request of include/galario_gb300.h."""
     _fields_ = [("image", P), ("intensity", P), ("nr", I32), ("Rmin", D), ("dR", D),
                 ("inc", D), ("nxy", I32), ("dxy", D), ("dRA", D), ("dDec", D), ("PA", D),
-                ("data", P), ("pb_fwhm", D)]
+                ("data", P), ("pb_fwhm", D), ("full_plane", I32)]
 
 
 class GalOpts(ct.Structure):

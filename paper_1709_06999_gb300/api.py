@@ -57,7 +57,8 @@ class Request:
 
     def __init__(self, obs: "Observation", *, image=None, intensity=None, dxy: float,
                  nxy: int | None = None, dRA: float = 0.0, dDec: float = 0.0, PA: float = 0.0,
-                 Rmin: float = 0.0, dR: float = 0.0, inc: float = 0.0, pb_fwhm: float = 0.0):
+                 Rmin: float = 0.0, dR: float = 0.0, inc: float = 0.0, pb_fwhm: float = 0.0,
+                 full_plane: bool = False):
         if (image is None) == (intensity is None):
             raise ValueError("give exactly one of image and intensity")
         self.obs, self.image, self.intensity = obs, image, intensity
@@ -70,6 +71,7 @@ class Request:
         self.nxy, self.dxy, self.dRA, self.dDec, self.PA = int(nxy), dxy, dRA, dDec, PA
         self.Rmin, self.dR, self.inc = Rmin, dR, inc
         self.pb_fwhm = pb_fwhm
+        self.full_plane = bool(full_plane)
 
     def _struct(self, ctx: "Context"):
         dt = self.obs.dtype
@@ -80,13 +82,13 @@ class Request:
             keep = img
             return _native.GalRequest(img.data_ptr(), None, 0, 0.0, 0.0, 0.0, self.nxy, self.dxy,
                                       self.dRA, self.dDec, self.PA, self.obs.handle.value,
-                                      self.pb_fwhm), keep
+                                      self.pb_fwhm, int(self.full_plane)), keep
         I = ctx._dev(self.intensity).contiguous()
         if I.dtype != dt:
             raise TypeError("intensity dtype must match the observation's")
         return _native.GalRequest(None, I.data_ptr(), I.numel(), self.Rmin, self.dR, self.inc,
                                   self.nxy, self.dxy, self.dRA, self.dDec, self.PA,
-                                  self.obs.handle.value, self.pb_fwhm), I
+                                  self.obs.handle.value, self.pb_fwhm, int(self.full_plane)), I
 
 
 def _request_array(ctx, requests):
@@ -483,12 +485,12 @@ class Server:
         if req.image is not None:
             t = req.image.to(self.device).contiguous()
             st = _native.GalRequest(t.data_ptr(), None, 0, 0.0, 0.0, 0.0, req.nxy, req.dxy,
-                                    req.dRA, req.dDec, req.PA, req.obs.handle.value, req.pb_fwhm)
+                                    req.dRA, req.dDec, req.PA, req.obs.handle.value, req.pb_fwhm, int(req.full_plane))
         else:
             t = req.intensity.to(self.device).contiguous()
             st = _native.GalRequest(None, t.data_ptr(), t.numel(), req.Rmin, req.dR, req.inc,
                                     req.nxy, req.dxy, req.dRA, req.dDec, req.PA,
-                                    req.obs.handle.value, req.pb_fwhm)
+                                    req.obs.handle.value, req.pb_fwhm, int(req.full_plane))
         if t.dtype != req.obs.dtype:
             raise TypeError("model dtype must match the observation's")
         return st, t

@@ -679,7 +679,11 @@ int check_request(gal_ctx* ctx, const gal_request& r) {
   GAL_TRY(check_geometry(r.nxy, r.dxy));
   if (!std::isfinite(r.dRA) || !std::isfinite(r.dDec) || !std::isfinite(r.PA)) return GAL_E_INVAL;
   if (!(r.pb_fwhm >= 0.0) || !std::isfinite(r.pb_fwhm)) return GAL_E_INVAL;
+  if (r.full_plane != 0 && r.full_plane != 1) return GAL_E_INVAL;
   const size_t rb = (size_t)d->real_bytes;
+  if (r.full_plane && !(rb == 8 ? gal::Plane<double>::supported(r.nxy)
+                                : gal::Plane<float>::supported(r.nxy)))
+    return GAL_E_INVAL;
   if ((r.image != nullptr) == (r.intensity != nullptr)) return GAL_E_INVAL;
   if (r.image) {
     if (!aligned(r.image, 2 * rb)) return GAL_E_INVAL;
@@ -739,14 +743,25 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
     b.M = d->M;
     b.chi2_out = chi2_out + i;
     b.edge = bd.r0 == 0;
-    b.grid = p ? chi2_gather_shape<double>(ctx, bd, &b.wbytes)
-               : chi2_gather_shape<float>(ctx, bd, &b.wbytes);
     const size_t cb = 2 * (size_t)d->real_bytes;  // complex value
+    b.full = r.full_plane == 1;
+    if (b.full) {  // the single full-plane call's window and gather shape
+      b.ncol = gal::full_cols(bd, r.nxy).W;
+      b.wbytes = round_up((size_t)bd.nrw * b.ncol * cb, 16);
+      if (b.wbytes > kWindowSmem) b.wbytes = 0;
+      b.grid = ctx->num_sms * (p ? gal::Plane<double>::gather_blocks_per_sm(true, b.wbytes)
+                                 : gal::Plane<float>::gather_blocks_per_sm(true, b.wbytes));
+      if (b.grid > ctx->partials_len) b.grid = ctx->partials_len;
+    } else {
+      b.ncol = bd.Kc;
+      b.grid = p ? chi2_gather_shape<double>(ctx, bd, &b.wbytes)
+                 : chi2_gather_shape<float>(ctx, bd, &b.wbytes);
+    }
     Off o;
     o.f1 = bytes;
-    bytes = round_up(bytes + (size_t)r.nxy * bd.Kc * cb, 256);
+    bytes = round_up(bytes + (size_t)r.nxy * b.ncol * cb, 256);
     o.gw = bytes;
-    bytes = round_up(bytes + round_up((size_t)bd.nrw * bd.Kc * cb, 16) + 16, 256);
+    bytes = round_up(bytes + round_up((size_t)bd.nrw * b.ncol * cb, 16) + 16, 256);
     o.part = bytes;
     bytes = round_up(bytes + sizeof(double) * (size_t)b.grid, 256);
     o.bm = 0;
@@ -837,6 +852,7 @@ int enqueue_rest(gal_ctx* ctx, const gal_request* reqs, const BatchPlan& pl, dou
     const gal::SweepParams sp{r.Rmin, r.dR, r.dxy, r.inc, r.nr};
     CallOpts o;
     o.pb_fwhm = r.pb_fwhm;
+    o.full = r.full_plane == 1;
     if (r.data->real_bytes == 8)
       GAL_TRY(chi2_impl<double>(ctx, static_cast<const double*>(r.image),
                                 static_cast<const double*>(r.intensity), sp, r.nxy, r.dxy, r.dRA,
@@ -966,7 +982,7 @@ bool same_structure(const std::vector<gal_request>& a, const gal_request* b, int
   for (int i = 0; i < n; ++i)
     if (a[i].data != b[i].data || a[i].nxy != b[i].nxy ||
         (a[i].image == nullptr) != (b[i].image == nullptr) ||
-        (a[i].pb_fwhm > 0.0) != (b[i].pb_fwhm > 0.0))
+        (a[i].pb_fwhm > 0.0) != (b[i].pb_fwhm > 0.0) || a[i].full_plane != b[i].full_plane)
       return false;
   return true;
 }

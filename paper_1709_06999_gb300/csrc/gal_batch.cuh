@@ -10,7 +10,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "gal_fft3_launch.cuh"
+#include "gal_plane.cuh"
 
 namespace gal {
 
@@ -68,6 +68,24 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
   return cudaGetLastError();
 }
 
+// full-plane rows: the chunk `idx[0..n)`, all of length 2^LG, all swept or
+// all images (16-byte aligned, staged by bulk copies); beam tables, if any,
+// were computed earlier in the stream
+template <typename T, int LG, bool SWEEP>
+cudaError_t rows_full(const BatchItem* it, const int* idx, int n, const void* tw, int* err,
+                      const BatchShape& sh, cudaStream_t st) {
+  using C = cplx_t<T>;
+  Jobs<RowJob<T>, kBatchJobs> jb{};
+  for (int k = 0; k < n; ++k) {
+    const BatchItem& b = it[idx[k]];
+    jb.j[k] = RowJob<T>{static_cast<const T*>(b.image), static_cast<const T*>(b.I),
+                        SWEEP ? sweep_cast<T>(b.sp) : SweepT<T>{}, static_cast<C*>(b.F1), b.rho2,
+                        b.S, static_cast<const T*>(b.beam)};
+  }
+  if constexpr (SWEEP) return launch_row_c2c<T, LG, true, kBatchJobs>(jb, n, sh.row_blocks, false, tw, st);
+  else return launch_row_c2c_tma<T, LG, kBatchJobs>(jb, n, sh.row_blocks, false, tw, err, st);
+}
+
 template <typename T, int LG>
 cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cudaStream_t st) {
   using C = cplx_t<T>;
@@ -82,8 +100,8 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
   for (int k = 0; k < n; ++k) {
     const BatchItem& b = it[idx[k]];
     jb.j[k] = ColJob<T>{static_cast<const C*>(b.F1), static_cast<C*>(b.Gw), b.rho2, b.S,
-                        /*full=*/0};
-    kc = b.Kc > kc ? b.Kc : kc;
+                        b.full ? 1 : 0};
+    kc = b.ncol > kc ? b.ncol : kc;
   }
   int x = (kc + SH::G - 1) / SH::G;
   const int cap = 2 * current_device_sms();
@@ -92,7 +110,7 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
   return cudaGetLastError();
 }
 
-template <typename T, bool SMEM, bool EDGE>
+template <typename T, bool SMEM, bool EDGE, bool FULL>
 cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStream_t st) {
   using C = cplx_t<T>;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -109,10 +127,10 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
     smem = b.wbytes > smem ? b.wbytes : smem;
   }
   if (!SMEM) smem = 0;
-  constexpr auto kern = gather_kernel<T, true, SMEM, EDGE, kBatchJobs>;
+  constexpr auto kern = gather_kernel<T, true, SMEM, EDGE, kBatchJobs, false, FULL>;
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
-  const int threads = gather_threads<SMEM>();
+  const int threads = gather_threads<SMEM, FULL>();
   kern<<<dim3(grid, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
   return cudaGetLastError();
 }
@@ -184,9 +202,24 @@ template <typename T>
 cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* tw, int* err,
                                  const BatchShape& sh, int* launches, cudaStream_t st) {
   auto pick = [](const BatchItem&) { return true; };
-  auto key = [](const BatchItem& b) { return b.N * 4 + (b.beam ? 2 : 0) + (b.I ? 1 : 0); };
+  auto key = [](const BatchItem& b) {
+    return b.N * 8 + (b.full ? 4 : 0) + (b.beam ? 2 : 0) + (b.I ? 1 : 0);
+  };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
     const int lg = ilog2i(b0.N);
+    if (b0.full) {  // complex-to-complex rows of length N
+      const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg, [&](auto L) {
+        constexpr int LG = decltype(L)::value;
+        if constexpr (LG > plane_max_lg<T>()) {
+          return cudaErrorNotSupported;
+        } else {
+          return b0.I ? batch::rows_full<T, LG, true>(it, idx, m, tw[lg], err, sh, st)
+                      : batch::rows_full<T, LG, false>(it, idx, m, tw[lg], err, sh, st);
+        }
+      });
+      if (!e) ++*launches;
+      return e;
+    }
     const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg - 1, [&](auto L) {
       constexpr int LG = decltype(L)::value;
       if constexpr (LG > 12) {
@@ -230,16 +263,19 @@ cudaError_t BatchLaunch<T>::gather(const BatchItem* it, int n, const BatchShape&
   auto pick = [](const BatchItem&) { return true; };
   // one launch shape per chunk: variant and blocks per request
   auto key = [](const BatchItem& b) {
-    return (int64_t)b.grid * 4 + (b.wbytes ? 2 : 0) + (b.edge ? 1 : 0);
+    return (int64_t)b.grid * 8 + (b.full ? 4 : 0) + (b.wbytes ? 2 : 0) + (b.edge ? 1 : 0);
   };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
     cudaError_t e;
-    if (b0.wbytes)
-      e = b0.edge ? batch::gather<T, true, true>(it, idx, m, b0.grid, st)
-                  : batch::gather<T, true, false>(it, idx, m, b0.grid, st);
-    else
-      e = b0.edge ? batch::gather<T, false, true>(it, idx, m, b0.grid, st)
-                  : batch::gather<T, false, false>(it, idx, m, b0.grid, st);
+    auto go = [&](auto full_c) {
+      constexpr bool F = decltype(full_c)::value;
+      if (b0.wbytes)
+        return b0.edge ? batch::gather<T, true, true, F>(it, idx, m, b0.grid, st)
+                       : batch::gather<T, true, false, F>(it, idx, m, b0.grid, st);
+      return b0.edge ? batch::gather<T, false, true, F>(it, idx, m, b0.grid, st)
+                     : batch::gather<T, false, false, F>(it, idx, m, b0.grid, st);
+    };
+    e = b0.full ? go(std::true_type{}) : go(std::false_type{});
     if (!e) ++*launches;
     return e;
   });

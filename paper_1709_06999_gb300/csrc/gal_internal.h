@@ -131,6 +131,8 @@ struct BatchItem {
   int grid;            // gather blocks (those of a single call of this request)
   void* beam;          // workspace: the request's 2N beam factors (null: no beam)
   BeamParams bp;       // their parameters
+  bool full;           // full-plane spectrum (complex-to-complex rows, no fold)
+  int ncol;            // window columns: Kc, or full_cols(...).W for the full plane
 };
 
 // Launch shape of the batched passes.  Results do not depend on it (every

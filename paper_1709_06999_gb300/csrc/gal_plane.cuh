@@ -63,11 +63,12 @@ template <typename T, int L> struct C2CRow {
 // its halves swapped.  Pruned, X[j] and X[N - j] come from one evaluation of
 // the last stage (pruned_pair3); otherwise the whole transform is kept.
 // The beam tables, when given, multiply each pixel as in the half-plane pass.
-template <typename T, int LG, bool SWEEP>
+template <typename T, int LG, bool SWEEP, int K = 1>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads,
                                   min_blocks_128regs<Shape3<T, (1 << LG), (1 << 30)>::threads>())
-row_c2c_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __restrict__ tw) {
+row_c2c_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw) {
   using C = cplx_t<T>;
+  const RowJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   grid_dep_launch();  // the column pass may be scheduled as our blocks retire
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
@@ -121,12 +122,13 @@ row_c2c_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __restrict
 // registers and released at once, so the transform's two buffers are
 // separate.  A wait that times out (never expected) sets bit 2 of *err,
 // drains the copies in flight (bounded) and ends the block.
-template <typename T, int LG>
+template <typename T, int LG, int K = 1>
 __global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << LG)>::threads,
                                   min_blocks_128regs<Shape3<T, (1 << LG), (1 << LG)>::threads>())
-row_c2c_tma_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __restrict__ tw,
-                   int* __restrict__ err) {
+row_c2c_tma_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs,
+                   const cplx_t<T>* __restrict__ tw, int* __restrict__ err) {
   using C = cplx_t<T>;
+  const RowJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   grid_dep_launch();  // the column pass may be scheduled as our blocks retire
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, N>;
@@ -209,12 +211,17 @@ row_c2c_tma_kernel(const __grid_constant__ RowJob<T> jb, const cplx_t<T>* __rest
   }
 }
 
-template <typename T, int LG, bool SWEEP>
-cudaError_t launch_row_c2c(const RowJob<T>& jb, const void* tw, cudaStream_t st) {
+// Launchers of the full-plane row pass over n jobs (grid row y = job y).  Each
+// job gets the GPU's resident blocks times `scale`, shared by the n jobs, as
+// persistent blocks; `dep`: launch as a programmatic dependent (the jobs
+// carry beam tables computed just before, single calls only).
+template <typename T, int LG, bool SWEEP, int K>
+cudaError_t launch_row_c2c(const Jobs<RowJob<T>, K>& jb, int n, int scale, bool dep,
+                           const void* tw, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, (1 << 30)>;
-  constexpr auto kern = row_c2c_kernel<T, LG, SWEEP>;
+  constexpr auto kern = row_c2c_kernel<T, LG, SWEEP, K>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -222,22 +229,24 @@ cudaError_t launch_row_c2c(const RowJob<T>& jb, const void* tw, cudaStream_t st)
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
   if (e) return e;
   if (per_sm < 1) per_sm = 1;
-  int grid = per_sm * current_device_sms();
+  int x = (per_sm * current_device_sms() * (scale < 1 ? 1 : scale) + n - 1) / n;
   const int need = (N + SH::G - 1) / SH::G;
-  if (grid > need) grid = need;
-  if (jb.beam)  // follows beam_table_kernel: start early, wait for the tables in the kernel
-    return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb,
+  if (x > need) x = need;
+  if (x < 1) x = 1;
+  if (dep)
+    return launch_dependent(kern, dim3(x, n), dim3(SH::threads), smem, st, jb,
                             static_cast<const C*>(tw));
-  kern<<<grid, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw));
+  kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, static_cast<const C*>(tw));
   return cudaGetLastError();
 }
 
-template <typename T, int LG>
-cudaError_t launch_row_c2c_tma(const RowJob<T>& jb, const void* tw, int* err, cudaStream_t st) {
+template <typename T, int LG, int K>
+cudaError_t launch_row_c2c_tma(const Jobs<RowJob<T>, K>& jb, int n, int scale, bool dep,
+                               const void* tw, int* err, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
   using SH = Shape3<T, N, N>;
-  constexpr auto kern = row_c2c_tma_kernel<T, LG>;
+  constexpr auto kern = row_c2c_tma_kernel<T, LG, K>;
   const size_t smem = 128 + (size_t)2 * SH::G * N * sizeof(T) + (size_t)2 * SH::G * SH::RS * sizeof(C);
   cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -245,12 +254,13 @@ cudaError_t launch_row_c2c_tma(const RowJob<T>& jb, const void* tw, int* err, cu
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
   if (e) return e;
   if (per_sm < 1) per_sm = 1;
-  int grid = per_sm * current_device_sms();
-  if (grid > N / SH::G) grid = N / SH::G;
-  if (jb.beam)  // follows beam_table_kernel: start early, wait for the tables in the kernel
-    return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb,
+  int x = (per_sm * current_device_sms() * (scale < 1 ? 1 : scale) + n - 1) / n;
+  if (x > N / SH::G) x = N / SH::G;
+  if (x < 1) x = 1;
+  if (dep)
+    return launch_dependent(kern, dim3(x, n), dim3(SH::threads), smem, st, jb,
                             static_cast<const C*>(tw), err);
-  kern<<<grid, SH::threads, smem, st>>>(jb, static_cast<const C*>(tw), err);
+  kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, static_cast<const C*>(tw), err);
   return cudaGetLastError();
 }
 
@@ -262,9 +272,12 @@ cudaError_t row_c2c_switch(int lg, const RowJob<T>& jb, int mode, const void* tw
     return cudaErrorNotSupported;
   } else {
     if (lg == LG) {
-      if (mode == 0) return launch_row_c2c_tma<T, LG>(jb, tw, err, st);
-      if (mode == 2) return launch_row_c2c<T, LG, true>(jb, tw, st);
-      return launch_row_c2c<T, LG, false>(jb, tw, st);
+      Jobs<RowJob<T>, 1> j1;
+      j1.j[0] = jb;
+      const bool dep = jb.beam != nullptr;
+      if (mode == 0) return launch_row_c2c_tma<T, LG, 1>(j1, 1, 1, dep, tw, err, st);
+      if (mode == 2) return launch_row_c2c<T, LG, true, 1>(j1, 1, 1, dep, tw, st);
+      return launch_row_c2c<T, LG, false, 1>(j1, 1, 1, dep, tw, st);
     }
     return row_c2c_switch<T, LG + 1>(lg, jb, mode, tw, err, st);
   }

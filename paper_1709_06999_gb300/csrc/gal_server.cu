@@ -57,7 +57,9 @@ int pow2_side(int n) { return n >= 4 && n <= 8192 && (n & (n - 1)) == 0; }
 size_t need_bytes(const gal_request& r, int real_bytes) {
   const size_t spec = (size_t)r.nxy * (size_t)(r.nxy / 2 + 1) * 2 * (size_t)real_bytes;
   const size_t beam = r.pb_fwhm > 0.0 ? 2 * (size_t)r.nxy * (size_t)real_bytes : 0;
-  return 3 * spec + beam;
+  // the full plane keeps up to nxy columns in the row-pass output
+  const size_t full = r.full_plane ? (size_t)r.nxy * (size_t)r.nxy * 2 * (size_t)real_bytes : 0;
+  return 3 * spec + beam + full;
 }
 
 }  // namespace
@@ -133,7 +135,7 @@ int gal_server::launch(Slot& s, std::vector<Pending>& grp) {
   int st;
   if (n == 1) {
     const gal_request& r = grp[0].req;
-    const gal_opts o{r.pb_fwhm, 0};  // a request's only option: its primary beam
+    const gal_opts o{r.pb_fwhm, r.full_plane};  // the request's options
     if (grp[0].prec == 0) {
       st = r.image ? gal_chi2_image_ex_f32(s.ctx, static_cast<const float*>(r.image), r.nxy,
                                            r.dxy, r.dRA, r.dDec, r.PA, &o, r.data, s.d_out, s.st)
@@ -332,6 +334,7 @@ static int make_pending(const gal_request* req, Pending* p) {
   if ((req->image != nullptr) == (req->intensity != nullptr)) return GAL_E_INVAL;
   if (!pow2_side(req->nxy) || !(req->dxy > 0.0)) return GAL_E_INVAL;
   if (!(req->pb_fwhm >= 0.0) || !std::isfinite(req->pb_fwhm)) return GAL_E_INVAL;
+  if (req->full_plane != 0 && req->full_plane != 1) return GAL_E_INVAL;
   p->req = *req;
   p->prec = rb == 8 ? 1 : 0;
   p->need = need_bytes(*req, rb);

@@ -28,10 +28,20 @@ def make_obs(ctx, u, v, w, nre, nim, dt):
 
 
 def single(ctx, r: Request):
+    kw = dict(pb_fwhm=r.pb_fwhm, full_plane=r.full_plane)
     if r.image is not None:
-        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, pb_fwhm=r.pb_fwhm)
+        return ctx.chi2_image(r.image, r.dxy, r.obs, r.dRA, r.dDec, r.PA, **kw)
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, r.obs, r.inc, r.dRA, r.dDec,
-                            r.PA, pb_fwhm=r.pb_fwhm)
+                            r.PA, **kw)
+
+
+def clone(r: Request, **kw):
+    """The same request with some fields replaced."""
+    f = dict(image=r.image, intensity=r.intensity, nxy=r.nxy, dxy=r.dxy, dRA=r.dRA, dDec=r.dDec,
+             PA=r.PA, Rmin=r.Rmin, dR=r.dR, inc=r.inc, pb_fwhm=r.pb_fwhm,
+             full_plane=r.full_plane)
+    f.update(kw)
+    return Request(r.obs, **f)
 
 
 def with_beams(reqs):
@@ -286,4 +296,77 @@ def test_invalid_beam_in_batch_launches_nothing():
         with pytest.raises(GalError):
             ctx.chi2_batch(list(reqs) + [Request(r.obs, image=r.image, intensity=r.intensity,
                                                  nxy=r.nxy, dxy=r.dxy, pb_fwhm=bad)])
+    assert ctx.launch_count() == n0
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_batch_full_plane_equals_single_calls_bitwise(dt):
+    """Full-plane requests (every other one, some with a beam) batched with
+    half-plane ones: bitwise the single calls with the same options."""
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, dt, seed=23, n_img=8, n_prof=5)
+    reqs = [clone(r, full_plane=(k % 2 == 0),
+                  pb_fwhm=0.0 if k % 3 == 2 else (0.35 + 0.03 * k) * r.nxy * r.dxy)
+            for k, r in enumerate(reqs)]
+    got = ctx.chi2_batch(reqs)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    assert torch.equal(got, want), (got - want).abs().max().item()
+    # and within rounding of the half-plane results (the C2C/R2C check) where
+    # every point lies inside the grid: beyond it the two paths clamp to
+    # different node ranges (-N/2..N/2-1 against 0..N/2 with the fold)
+    half = ctx.chi2_batch([clone(r, full_plane=False) for r in reqs])
+    inside = 0
+    for k, r in enumerate(reqs):
+        u, v = (t.double() for t in r.obs._tensors[:2])
+        rho = torch.sqrt(torch.max(u * u + v * v)).item()
+        if rho * r.nxy * r.dxy < r.nxy / 2 - 1:
+            inside += 1
+            rel = abs(got[k].item() - half[k].item()) / abs(half[k].item())
+            assert rel <= 2 * TOL_CHI2[dt], (k, rel)
+    assert inside >= 3
+
+
+def test_batch_full_plane_matches_oracle():
+    ctx = Context(0)
+    dt = torch.float32
+    reqs, keep = mixed_requests(ctx, dt, seed=25, n_img=3, n_prof=2)
+    reqs = [clone(r, full_plane=True, pb_fwhm=0.5 * r.nxy * r.dxy if k % 2 else 0.0)
+            for k, r in enumerate(reqs)]
+    got = ctx.chi2_batch(reqs).cpu().numpy()
+    for r, g in zip(reqs, got):
+        u, v, re, im, w = (t.double().cpu().numpy() for t in r.obs._tensors)
+        kw = dict(pb_fwhm=r.pb_fwhm, full_plane=True)
+        if r.image is not None:
+            ref = oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w,
+                                    r.dRA, r.dDec, r.PA, **kw)
+        else:
+            ref = oracle.chi2_profile(r.intensity.double().cpu().numpy(), r.Rmin, r.dR, r.nxy,
+                                      r.dxy, u, v, re, im, w, r.dRA, r.dDec, r.PA, r.inc, **kw)
+        assert abs(g - ref) <= TOL_CHI2[dt] * abs(ref), (g, ref)
+
+
+def test_graph_full_plane_replay_update_and_structure():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=27, n_img=4, n_prof=2)
+    reqs = [clone(r, full_plane=(k % 2 == 1)) for k, r in enumerate(reqs)]
+    g = ctx.capture_batch(reqs)
+    out = g.launch().clone()
+    assert torch.equal(out, torch.stack([single(ctx, r) for r in reqs]))
+    new = [clone(r, PA=r.PA + 0.7, dRA=r.dRA - 1e-7) for r in reqs]
+    g.update(new)
+    out = g.launch().clone()
+    assert torch.equal(out, torch.stack([single(ctx, r) for r in new]))
+    with pytest.raises(GalError):  # switching a request's spectrum path changes the structure
+        g.update([clone(new[0], full_plane=not new[0].full_plane)] + new[1:])
+    g.close()
+
+
+def test_invalid_full_plane_in_batch_launches_nothing():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=29, n_img=2, n_prof=1)
+    n0 = ctx.launch_count()
+    r = next(r for r in reqs if r.image is not None)
+    small = torch.zeros((8, 8), dtype=torch.float32, device="cuda")  # below the f32 full-plane range
+    with pytest.raises(GalError):
+        ctx.chi2_batch(list(reqs) + [Request(r.obs, image=small, dxy=r.dxy, full_plane=True)])
     assert ctx.launch_count() == n0

@@ -54,10 +54,11 @@ def requests(data, dt, n, seed=1, sizes=(32, 64, 128, 256, 512)):
 
 def single(ctx, r):
     obs = ctx.register(*r.obs._tensors)
+    kw = dict(pb_fwhm=r.pb_fwhm, full_plane=r.full_plane)
     if r.image is not None:
-        return ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA, pb_fwhm=r.pb_fwhm).item()
+        return ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA, **kw).item()
     return ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, obs, r.inc, r.dRA, r.dDec,
-                            r.PA, pb_fwhm=r.pb_fwhm).item()
+                            r.PA, **kw).item()
 
 
 @pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
@@ -82,14 +83,16 @@ def test_alone_equals_mix(dt):
 
 
 def test_beams_alone_equal_mix():
-    """Requests with per-request primary beams, served alone and in a burst:
-    bitwise equal to each other and to single calls."""
+    """Requests with per-request primary beams and some on the full-plane
+    spectrum, served alone and in a burst: bitwise equal to each other and to
+    single calls."""
     dt = torch.float32
     srv = Server(0, hbm_budget=8 * 10**9, slots=4, max_batch=8)
     data = datasets(srv, 4, dt, seed=8)
     reqs = []
     for k, r in enumerate(requests(data, dt, 24, seed=9)):
         r.pb_fwhm = 0.0 if k % 4 == 3 else (0.4 + 0.02 * k) * r.nxy * r.dxy
+        r.full_plane = k % 3 == 1
         reqs.append(r)
     alone = [srv.wait(srv.submit(r))[0] for r in reqs]
     tickets = srv.submit_many(reqs)
