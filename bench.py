@@ -43,7 +43,7 @@ STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
 KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1, 0>", 2: "col_fft3_kernel<float, 12, 1>",
            3: "gather_kernel<float, 1, 1, 0, 1, 0, 0>"}
 # the full-plane (complex-to-complex) spectrum path
-KERNELS_FULL = {1: "row_c2c_tma_kernel<float, 12>", 2: "col_fft3_kernel<float, 12, 1>",
+KERNELS_FULL = {1: "row_c2c_tma_kernel<float, 12, 1>", 2: "col_fft3_kernel<float, 12, 1>",
                 3: "gather_kernel<float, 1, 1, 0, 1, 0, 1>"}
 # primary beam of a 12 m antenna at 100 GHz: FWHM = K lambda / D, K = 1.13
 PB_FWHM = 1.13 * (299792458.0 / 100e9) / 12.0
