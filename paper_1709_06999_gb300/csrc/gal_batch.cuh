@@ -90,7 +90,7 @@ template <typename T, int LG>
 cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = Shape3<T, N, (1 << 30)>;
+  using SH = ColShape3<T, N>;
   constexpr auto kern = col_fft3_kernel<T, LG, kBatchJobs>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);

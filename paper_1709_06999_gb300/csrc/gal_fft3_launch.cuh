@@ -49,7 +49,7 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
                         int kc_hint, bool full, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = Shape3<T, N, (1 << 30)>;
+  using SH = ColShape3<T, N>;
   constexpr auto kern = col_fft3_kernel<T, LG, 1>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);

@@ -359,11 +359,11 @@ template <typename C> __device__ __forceinline__ C r2c_unpack(C zk, C zmk, C w) 
 // Launch shape of the length-L passes: G sequences per block (at least 128
 // threads), each with a shared-memory region of RS complex (padded, rounded
 // to 16 bytes so that bulk copies into it stay aligned).
-template <typename T, int L, int NSEQ> struct Shape3 {
+template <typename T, int L, int NSEQ, int MINT = 128> struct Shape3 {
   using C = cplx_t<T>;
   static constexpr int V = FftV<T>::V;
   using P = P3<L, V>;
-  static constexpr int G0 = P::T >= 128 ? 1 : 128 / P::T;
+  static constexpr int G0 = P::T >= MINT ? 1 : MINT / P::T;
   static constexpr int G = G0 < NSEQ ? G0 : NSEQ;
   static constexpr int threads = G * P::T;
   static constexpr int RS = (P::padded * (int)sizeof(C) + 15) / 16 * 16 / (int)sizeof(C);
@@ -446,9 +446,18 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       C* o = in == A ? B : A;
       store_full<M, V>(v, o, t);
       __syncthreads();
-      for (int k = t; k < bd.Kc; k += TT)
-        out[(size_t)k * N] =
-            r2c_unpack(o[pad3<V>(k & (M - 1))], o[pad3<V>((M - k) & (M - 1))], __ldg(tw + k));
+      // the G rows of the group are consecutive and all in shared memory
+      // (row gg's buffer lies (gg - g) RS from ours): unpack bin by bin with
+      // the G rows side by side, so each store fills G adjacent values of a
+      // column instead of one value per sector
+      const C* o0 = o - (size_t)g * RS;
+      C* out0 = out - g;
+      for (int q = threadIdx.x; q < bd.Kc * G; q += G * TT) {
+        const int k = q / G, gg = q - k * G;
+        const C* og = o0 + (size_t)gg * RS;
+        out0[(size_t)k * N + gg] =
+            r2c_unpack(og[pad3<V>(k & (M - 1))], og[pad3<V>((M - k) & (M - 1))], __ldg(tw + k));
+      }
     }
   };
   if constexpr (TMA) {
@@ -532,8 +541,14 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
 // of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
 // r0 + nrw - 1 are written to the window Gw (nrw x Kc).  When the window is
 // pruned, only the kept frequencies +-j are evaluated.
+// Blocks have at least 256 threads, so short columns come G >= 4 to a block:
+// an unpruned window is then written a row at a time with the block's G
+// adjacent columns side by side (whole 32-byte sectors, not one 8-byte value
+// per sector).
+template <typename T, int L> using ColShape3 = Shape3<T, L, (1 << 30), 256>;
+
 template <typename T, int LG, int K>
-__global__ void __launch_bounds__(Shape3<T, (1 << LG), (1 << 30)>::threads)
+__global__ void __launch_bounds__(ColShape3<T, (1 << LG)>::threads)
 col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw) {
   const ColJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   const cplx_t<T>* __restrict__ F1 = jb.F1;
@@ -543,7 +558,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   grid_dep_launch();  // the gather may start its prologue on the SMs we leave idle
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = Shape3<T, N, (1 << 30)>;
+  using SH = ColShape3<T, N>;
   using P = typename SH::P;
   constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -590,9 +605,14 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
       C* o = in == A ? B : A;
       store_full<N, V>(v, o, t);
       __syncthreads();
-      if (act)
-        for (int rr = t; rr < bd.nrw; rr += TT)
-          Gw[(size_t)rr * ncol + c] = o[pad3<V>((bd.r0 + rr + N / 2) & (N - 1))];
+      // every column of the group is in shared memory (group gg's output
+      // buffer lies (gg - g) RS from ours): write row by row, G columns side by side
+      const C* o0 = o - (size_t)g * RS;
+      for (int q = threadIdx.x; q < bd.nrw * G; q += G * TT) {
+        const int rr = q / G, gg = q - rr * G;
+        if (c0 + gg < ncol)
+          Gw[(size_t)rr * ncol + c0 + gg] = o0[(size_t)gg * RS + pad3<V>((bd.r0 + rr + N / 2) & (N - 1))];
+      }
     }
     __syncthreads();
   }
@@ -1381,7 +1401,7 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
 template <bool SMEM, bool FULL = false> constexpr int gather_threads() {
   return SMEM ? (FULL ? 1024 : 512) : 256;
 }
-template <bool SMEM, bool FULL> constexpr int gather_min_blocks() { return SMEM ? (FULL ? 1 : 2) : 3; }
+template <bool SMEM, bool FULL> constexpr int gather_min_blocks() { return SMEM ? (FULL ? 1 : 2) : 4; }
 
 template <typename T, bool CHI2, bool SMEM, bool EDGE, int K, bool MULTI = false, bool FULL = false>
 __global__ void __launch_bounds__(gather_threads<SMEM, FULL>(), gather_min_blocks<SMEM, FULL>())
