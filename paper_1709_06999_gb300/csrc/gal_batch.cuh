@@ -110,6 +110,11 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
   return cudaGetLastError();
 }
 
+// Each request keeps the block partition of its single call (`grid` virtual
+// blocks, one partial sum each); a launch runs kGatherFold of them per block
+// in turn, so a request's window is copied by a quarter as many blocks.
+constexpr int kGatherFold = 4;
+
 template <typename T, bool SMEM, bool EDGE, bool FULL>
 cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStream_t st) {
   using C = cplx_t<T>;
@@ -123,7 +128,7 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
                            static_cast<const T*>(b.u), static_cast<const T*>(b.v),
                            static_cast<const T*>(b.re), static_cast<const T*>(b.im),
                            static_cast<const T*>(b.w), b.M, vec, nullptr, b.partials,
-                           b.counter, b.chi2_out};
+                           b.counter, b.chi2_out, grid};
     smem = b.wbytes > smem ? b.wbytes : smem;
   }
   if (!SMEM) smem = 0;
@@ -131,7 +136,8 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
   const int threads = gather_threads<SMEM, FULL>();
-  kern<<<dim3(grid, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
+  const int blocks = (grid + kGatherFold - 1) / kGatherFold;
+  kern<<<dim3(blocks, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
   return cudaGetLastError();
 }
 

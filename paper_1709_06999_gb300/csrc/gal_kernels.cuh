@@ -740,9 +740,10 @@ template <typename T> struct GatherJob {
   int64_t M;
   int vec;              // all point arrays 16-byte aligned
   cplx_t<T>* vis;       // sample mode output
-  double* partials;     // chi2 mode: one slot per block of the request
+  double* partials;     // chi2 mode: one slot per (virtual) block of the request
   unsigned* counter;    // chi2 mode: last-block-done counter (self-resetting)
   double* chi2_out;
+  int vblocks = 0;      // batched launches: the request's virtual blocks (see gather_kernel)
 };
 
 // Offsets and amplitudes of the K copies of one model in a multi-source
@@ -1309,15 +1310,17 @@ template <typename T, bool CHI2> struct PointGroup {
 // Grid-stride layout of the vector groups: whole rounds of gstride groups,
 // then the remainder in equal contiguous slices, one per block (coalesced,
 // and no few blocks run a round more than the rest).
+// nblk blocks, this thread in block bid.
 struct GroupSplit {
-  int64_t nq, gstride, rounds, slice, rem_q;
-  __device__ __forceinline__ GroupSplit(int64_t M, int W, int vec) {
+  int64_t nq, gstride, rounds, slice, rem_q, gtid;
+  __device__ __forceinline__ GroupSplit(int64_t M, int W, int vec, int nblk, int bid) {
     nq = vec ? M / W : 0;
-    gstride = (int64_t)gridDim.x * blockDim.x;
+    gstride = (int64_t)nblk * blockDim.x;
     rounds = nq / gstride;
     const int64_t rem = nq - rounds * gstride;
-    slice = (rem + gridDim.x - 1) / gridDim.x;  // <= blockDim.x
-    rem_q = rounds * gstride + (int64_t)blockIdx.x * slice + threadIdx.x;
+    slice = (rem + nblk - 1) / nblk;  // <= blockDim.x
+    rem_q = rounds * gstride + (int64_t)bid * slice + threadIdx.x;
+    gtid = (int64_t)bid * blockDim.x + threadIdx.x;
   }
   __device__ __forceinline__ bool has_rem() const { return threadIdx.x < slice && rem_q < nq; }
 };
@@ -1331,14 +1334,13 @@ __device__ __forceinline__ void gather_points(const cplx_t<T>* __restrict__ G, c
                                               const T* __restrict__ im, const T* __restrict__ w,
                                               int64_t M, int vec, cplx_t<T>* __restrict__ vis,
                                               ACC& acc, const MultiPhase<T>* mp,
-                                              const PointGroup<T, CHI2>* pre) {
+                                              const PointGroup<T, CHI2>* pre, const GroupSplit& sp) {
   using C = cplx_t<T>;
   constexpr int W = Vec16<T>::W;
   auto point = [&](T uu, T vv) {
     return sample_point<SMEM, EDGE, MULTI, FULL>(G, win, p, uu, vv, mp);
   };
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const GroupSplit sp(M, W, vec);
+  const int64_t gtid = sp.gtid;
   auto compute = [&](const PointGroup<T, CHI2>& g, int64_t q) {  // the W points of group q
     const T(&uu)[W] = g.uu;
     const T(&vv)[W] = g.vv;
@@ -1426,32 +1428,44 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
   double* __restrict__ chi2_out = jb.chi2_out;
   const Bounds bd = block_bounds(rho2, p.Sd, p.N);
   const Window win = FULL ? make_window_full(bd, p.N) : make_window(bd, p.N);
-  typename Acc<T>::type acc;
+  // Virtual blocks: a batched launch may run fewer blocks than the request
+  // has partial sums (nvb).  Block b then evaluates virtual blocks b,
+  // b + gridDim.x, ... in turn, each exactly as block vb of a single call
+  // (same points in the same order, same partial sum), so batched and single
+  // results agree bit for bit while each block copies the window only once.
+  const int nvb = K == 1 ? (int)gridDim.x : jb.vblocks;
   // The observation does not depend on the column pass: while that pass
   // finishes, load this thread's first group into registers (when the grid
   // has a whole round) and pull its remainder group, if any, towards L2.
+  // (Single calls only: batched launches are not dependents.)
   constexpr int W = Vec16<T>::W;
-  const GroupSplit gs(M, W, vec);
+  const GroupSplit gs(M, W, vec, nvb, blockIdx.x);
   PointGroup<T, CHI2> g0;
-  const bool pre = gs.rounds > 0;  // uniform over the grid
-  if (pre) g0.load(u, v, re, im, w, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-  if (gs.has_rem()) {
-    const int64_t o = gs.rem_q * W;
-    prefetch_l2(u + o);
-    prefetch_l2(v + o);
-    if constexpr (CHI2) {
-      prefetch_l2(re + o);
-      prefetch_l2(im + o);
-      prefetch_l2(w + o);
+  const bool pre = K == 1 && gs.rounds > 0;  // uniform over the grid
+  if constexpr (K == 1) {
+    if (pre) g0.load(u, v, re, im, w, gs.gtid);
+    if (gs.has_rem()) {
+      const int64_t o = gs.rem_q * W;
+      prefetch_l2(u + o);
+      prefetch_l2(v + o);
+      if constexpr (CHI2) {
+        prefetch_l2(re + o);
+        prefetch_l2(im + o);
+        prefetch_l2(w + o);
+      }
     }
   }
-  const PointGroup<T, CHI2>* g0p = pre ? &g0 : nullptr;
   grid_dep_wait();  // the window is the column pass's output
+  C* sw = nullptr;
+  bool win_ok = true;
   if constexpr (SMEM) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    C* sw = reinterpret_cast<C*>(smem_raw);
+    sw = reinterpret_cast<C*>(smem_raw);
     const int nodes = bd.nrw * win.pitch;
-    if (nodes <= smem_nodes) {  // uniform over the grid; always true when sized by the host
+    // the host sizes the shared window from the same extent, so this always
+    // holds; otherwise the result is NaN rather than a read out of bounds
+    win_ok = nodes <= smem_nodes;  // uniform over the grid
+    if (win_ok) {
       // one bulk copy of the window (rounded up to 16 bytes; the window
       // buffer and the shared allocation both have the slack)
       __shared__ __align__(8) uint64_t wbar;
@@ -1468,30 +1482,40 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
         for (int i = threadIdx.x; i < nodes; i += blockDim.x) sw[i] = __ldg(Gw + i);
         __syncthreads();
       }
-      gather_points<T, CHI2, true, EDGE, MULTI, FULL>(sw, win, p, u, v, re, im, w, M, vec, vis, acc,
-                                                      mp, g0p);
-    } else {
-      // the host sizes the shared window from the same extent, so this is
-      // never taken; the result is NaN rather than a read out of bounds
-      const T nan = std::numeric_limits<T>::quiet_NaN();
-      if constexpr (CHI2) {
-        acc.add(nan);
-      } else {
-        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < M;
-             k += (int64_t)gridDim.x * blockDim.x)
-          vis[k] = mkc(nan, nan);
-      }
     }
+  }
+  __shared__ double ws[32];
+  auto run = [&](int vb, const GroupSplit& sp, const PointGroup<T, CHI2>* g0p) {
+    typename Acc<T>::type acc;
+    if constexpr (SMEM) {
+      if (win_ok) {
+        gather_points<T, CHI2, true, EDGE, MULTI, FULL>(sw, win, p, u, v, re, im, w, M, vec, vis,
+                                                        acc, mp, g0p, sp);
+      } else {
+        const T nan = std::numeric_limits<T>::quiet_NaN();
+        if constexpr (CHI2) {
+          acc.add(nan);
+        } else {
+          for (int64_t k = sp.gtid; k < M; k += sp.gstride) vis[k] = mkc(nan, nan);
+        }
+      }
+    } else {
+      gather_points<T, CHI2, false, EDGE, MULTI, FULL>(Gw, win, p, u, v, re, im, w, M, vec, vis,
+                                                       acc, mp, g0p, sp);
+    }
+    if constexpr (CHI2) {
+      const double bs = acc.block_total(ws);
+      if (threadIdx.x == 0) partials[vb] = bs;
+    }
+  };
+  if constexpr (K == 1) {
+    run(blockIdx.x, gs, pre ? &g0 : nullptr);
   } else {
-    gather_points<T, CHI2, false, EDGE, MULTI, FULL>(Gw, win, p, u, v, re, im, w, M, vec, vis, acc,
-                                                     mp, g0p);
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) run(vb, GroupSplit(M, W, vec, nvb, vb), nullptr);
   }
   if constexpr (CHI2) {
-    __shared__ double ws[32];
     __shared__ bool last;
-    const double bs = acc.block_total(ws);
     if (threadIdx.x == 0) {
-      partials[blockIdx.x] = bs;
       __threadfence();
       const unsigned prev = atomicAdd(counter, 1u);
       last = (prev == gridDim.x - 1);
@@ -1500,7 +1524,7 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
     if (last) {
       __threadfence();
       AccD a;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a.add(__ldcg(partials + b));
+      for (int b = threadIdx.x; b < nvb; b += blockDim.x) a.add(__ldcg(partials + b));
       const double tot = block_sum(a.value(), ws);
       if (threadIdx.x == 0) {
         *chi2_out = tot;
