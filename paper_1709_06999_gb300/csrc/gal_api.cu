@@ -596,12 +596,15 @@ int chi2_image_host_async_t(gal_ctx* ctx, const T* image_host, int nxy, double d
   if (!aligned(chi2_host, sizeof(double))) return GAL_E_INVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!ctx->copy_stream) {
-    GAL_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    // the events and result slots first: copy_stream marks a complete set-up
     for (int s = 0; s < 2; ++s) {
-      GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_copied[s], cudaEventDisableTiming));
-      GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_done[s], cudaEventDisableTiming));
+      if (!ctx->pipe_copied[s])
+        GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_copied[s], cudaEventDisableTiming));
+      if (!ctx->pipe_done[s])
+        GAL_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pipe_done[s], cudaEventDisableTiming));
     }
-    GAL_CUDA(ctx, cudaMalloc(&ctx->pipe_chi2, 2 * sizeof(double)));
+    if (!ctx->pipe_chi2) GAL_CUDA(ctx, cudaMalloc(&ctx->pipe_chi2, 2 * sizeof(double)));
+    GAL_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
   }
   const int s = (int)(ctx->pipe_k & 1);
   const size_t bytes = (size_t)nxy * nxy * sizeof(T);
