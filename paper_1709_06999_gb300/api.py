@@ -73,6 +73,27 @@ class Request:
         self.pb_fwhm = pb_fwhm
         self.full_plane = bool(full_plane)
 
+    def __setattr__(self, name, value):
+        # any change of an argument drops the marshalled copy (_packed)
+        object.__setattr__(self, "_packed", None)
+        object.__setattr__(self, name, value)
+
+    def _pack(self, ctx: "Context"):
+        """The request as gal_request bytes and the tensor they point into.
+        Reused while no argument was reassigned and the (contiguous) tensor
+        still has the same storage on the context's device."""
+        t = self.image if self.image is not None else self.intensity
+        c = self._packed
+        if (c is not None and c[0] == ctx.device and c[1] == t.data_ptr()
+                and c[2] == self.obs.handle.value):  # an observation closed since: not reused
+            return c[3], c[4]
+        st, keep = self._struct(ctx)
+        b = bytes(st)
+        if keep is t:  # used in place, so its storage pointer identifies it
+            object.__setattr__(self, "_packed",
+                               (ctx.device, t.data_ptr(), self.obs.handle.value, b, keep))
+        return b, keep
+
     def _struct(self, ctx: "Context"):
         dt = self.obs.dtype
         if self.image is not None:
@@ -92,12 +113,14 @@ class Request:
 
 
 def _request_array(ctx, requests):
-    structs, keep = [], []
+    parts, keep = [], []
     for r in requests:
-        st, k = r._struct(ctx)
-        structs.append(st)
+        b, k = r._pack(ctx)
+        parts.append(b)
         keep.append(k)
-    arr = (_native.GalRequest * max(1, len(structs)))(*structs)
+    size = ct.sizeof(_native.GalRequest)
+    data = b"".join(parts) if parts else bytes(size)
+    arr = (_native.GalRequest * max(1, len(parts))).from_buffer_copy(data)
     return arr, keep
 
 
