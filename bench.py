@@ -416,14 +416,15 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
     r32, r64 = [], []
     for ch in cube:
         t32 = [d32(a) for a in (ch.u, ch.v, ch.noise_re, ch.noise_im, ch.w)]
-        o32 = ctx.register(*t32)
-        o64 = ctx.register(*[t.double() for t in t32])
+        o32 = ctx.register(*t32, z_order=True)
+        o64 = ctx.register(*[t.double() for t in t32], z_order=True)
         img = d32(ch.image)
         r32.append(Request(o32, image=img, dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec, PA=ch.PA))
         r64.append(Request(o64, image=img.double(), dxy=ch.dxy, dRA=ch.dRA, dDec=ch.dDec,
                            PA=ch.PA))
     sets["cube"] = (r32, r64, "128 Keplerian-disc channels, nxy U{512,1024,2048}, "
-                              "M_c U[1e5,2e6] (ALMA-like layout x channel frequency)")
+                              "M_c U[1e5,2e6] (ALMA-like layout x channel frequency), "
+                              "observations registered in Z-order")
     # the same channels, each through its own primary beam: FWHM 1.13 lambda_c / 12 m
     # (channel frequency: line at 100 GHz, channels 0.5 km/s apart, as in the cube)
     b32, b64 = [], []
@@ -437,8 +438,8 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
                                     "(FWHM 1.13 lambda_c / 12 m, applied in the row FFT)")
     q = synth.profile_problem(nxy=1024, M=1_000_000, nr=8192, seed=1)
     t32 = [d32(a) for a in (q.u, q.v, q.noise_re, q.noise_im, q.w)]
-    o32 = ctx.register(*t32)
-    o64 = ctx.register(*[t.double() for t in t32])
+    o32 = ctx.register(*t32, z_order=True)
+    o64 = ctx.register(*[t.double() for t in t32], z_order=True)
     w32, w64 = [], []
     for wp in synth.walker_params(64):
         I = d32(synth.ring_profile(8192, q.dR, q.Rmin, wp["r0"], wp["width"], wp["power"]))
@@ -447,7 +448,7 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
         w32.append(Request(o32, intensity=I, **kw))
         w64.append(Request(o64, intensity=I.double(), **kw))
     sets["walkers"] = (w32, w64, "64 ring-profile walkers, nxy 1024, nr 8192, one M=1e6 "
-                                 "observation shared")
+                                 "observation shared, registered in Z-order")
     res = {}
     for name, (a32, a64, desc) in sets.items():
         n = len(a32)

@@ -107,6 +107,27 @@ int gal_data_create_f32(gal_ctx* ctx, const float* u, const float* v, const floa
                         const float* im, const float* w, int64_t M, void* stream, gal_data** out);
 int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
                         const double* im, const double* w, int64_t M, void* stream, gal_data** out);
+/* Register an observation as gal_data_create_* does, from copies the handle
+ * owns, stored in Z-order (Morton order) of the uv plane: both axes quantised
+ * to 16 bits over [-rho, rho] (rho the largest finite baseline), the two cells
+ * bit-interleaved, points sorted stably by that key (non-finite points last).
+ * The chi-square (Sect. 3.1, Eq. chap6.eq:def.chi.square) is a sum over the
+ * points, so it is unchanged up to the rounding of the new order, and results
+ * are the same on every run.  Points close in the uv plane then sample
+ * neighbouring cells of the spectrum next to each other in memory, which
+ * matters when a model's kept spectrum is too large for shared memory and is
+ * read through L2.  u, v, re, im, w are read during the
+ * call only: u and v are copied to the host and ordered there (a radix sort),
+ * the five arrays gathered on `stream` into one device buffer of 5 M values
+ * (freed by gal_data_destroy); the call synchronises `stream`.  Same errors as
+ * gal_data_create_*, plus GAL_E_NOMEM when the host or device buffers cannot
+ * be allocated. */
+int gal_data_create_sorted_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
+                               const float* im, const float* w, int64_t M, void* stream,
+                               gal_data** out);
+int gal_data_create_sorted_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
+                               const double* im, const double* w, int64_t M, void* stream,
+                               gal_data** out);
 /* Register an observation whose baselines u_m, v_m are in metres, with the
  * frequency nu (Hz) of every visibility (lifts the single-frequency assumption
  * of Sect. 3: each visibility samples the model at its own u_m nu / c).  The

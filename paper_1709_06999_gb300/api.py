@@ -167,9 +167,13 @@ class Observation:
     alive.  Creation enqueues one reduction for the uv extent.
     """
 
-    def __init__(self, ctx: "Context", u, v, re, im, w, nu=None):
+    def __init__(self, ctx: "Context", u, v, re, im, w, nu=None, z_order=False):
         """u, v in wavelengths; or, with `nu` (Hz per visibility), in metres
-        (gal_data_create_freq_*: the library converts them once)."""
+        (gal_data_create_freq_*: the library converts them once).  z_order:
+        the library keeps copies in Z-order of the uv plane
+        (gal_data_create_sorted_*), the tensors are not kept."""
+        if z_order and nu is not None:
+            raise ValueError("z_order applies to observations in wavelengths")
         arrays = (u, v, re, im, w) if nu is None else (u, v, nu, re, im, w)
         tensors = [ctx._dev(t).contiguous() for t in arrays]
         m = tensors[0].numel()
@@ -180,13 +184,14 @@ class Observation:
         self.dtype = tensors[0].dtype
         sfx = _suffix(*tensors)
         h = ct.c_void_p()
-        name = f"gal_data_create_{sfx}" if nu is None else f"gal_data_create_freq_{sfx}"
+        name = (f"gal_data_create_freq_{sfx}" if nu is not None else
+                f"gal_data_create_sorted_{sfx}" if z_order else f"gal_data_create_{sfx}")
         fn = getattr(ctx.lib, name)
         _check(ctx.handle, fn(ctx.handle, *[t.data_ptr() for t in tensors], m, ctx._stream(), ct.byref(h)))
         self.handle = h
         # borrowed arrays stay alive with the handle (with nu, u and v live in
         # the library)
-        self._tensors = tensors if nu is None else tensors[3:]
+        self._tensors = [] if z_order else tensors if nu is None else tensors[3:]
 
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
@@ -260,8 +265,11 @@ class Context:
         """Register visibilities with baselines in metres and their frequencies (Hz)."""
         return Observation(self, u_m, v_m, re, im, w, nu=nu)
 
-    def register(self, u, v, re, im, w) -> Observation:
-        return Observation(self, u, v, re, im, w)
+    def register(self, u, v, re, im, w, z_order: bool = False) -> Observation:
+        """Register visibilities (u, v in wavelengths).  z_order=True keeps
+        library-owned copies ordered along the uv plane (faster gathers from
+        spectra too large for shared memory; chi-square equal up to rounding)."""
+        return Observation(self, u, v, re, im, w, z_order=z_order)
 
     # -- operations ---------------------------------------------------------
     def sweep(self, intensity, Rmin: float, dR: float, nxy: int, dxy: float, inc: float = 0.0,

@@ -18,6 +18,7 @@
 #include "../../include/galario_gb300.h"
 #include "gal_common.cuh"
 #include "gal_internal.h"
+#include "gal_reorder.h"
 
 namespace {
 
@@ -91,7 +92,8 @@ struct gal_data {
   const void *u = nullptr, *v = nullptr, *re = nullptr, *im = nullptr, *w = nullptr;
   double* rho2 = nullptr;  // device scalar: max(u^2 + v^2)
   double rho2_host = 0.0;  // the same value, read back once at registration
-  void* uv_own = nullptr;  // u, v in wavelengths when registered from metres (2 M values)
+  void* uv_own = nullptr;  // arrays the handle owns: u, v in wavelengths when registered
+                           // from metres, or all five when registered in Z-order
 };
 
 namespace {
@@ -563,6 +565,58 @@ int data_create_freq_t(gal_ctx* ctx, const T* u_m, const T* v_m, const T* nu, co
   return GAL_OK;
 }
 
+
+// Registration from copies in Z-order (gal_reorder.h): the order is computed
+// on the host from u and v, the five arrays are gathered into one buffer the
+// handle owns, then the copies are registered as usual.
+template <typename T>
+int data_create_sorted_t(gal_ctx* ctx, const T* u, const T* v, const T* re, const T* im,
+                         const T* w, int64_t M, void* stream, gal_data** out) {
+  if (!ctx || !out || M < 0) return GAL_E_INVAL;
+  if (M > 0 && (!u || !v || !re || !im || !w)) return GAL_E_INVAL;
+  for (const void* p : {(const void*)u, (const void*)v, (const void*)re, (const void*)im,
+                        (const void*)w})
+    if (!aligned(p, sizeof(T))) return GAL_E_INVAL;
+  if (M == 0) return data_create_t<T>(ctx, u, v, re, im, w, M, stream, out);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int64_t> perm;
+  try {
+    std::vector<T> hu((size_t)M), hv((size_t)M);
+    GAL_CUDA(ctx, cudaMemcpyAsync(hu.data(), u, sizeof(T) * (size_t)M, cudaMemcpyDeviceToHost, st));
+    GAL_CUDA(ctx, cudaMemcpyAsync(hv.data(), v, sizeof(T) * (size_t)M, cudaMemcpyDeviceToHost, st));
+    GAL_CUDA(ctx, cudaStreamSynchronize(st));
+    gal::z_order<T>(hu.data(), hv.data(), M, perm);
+  } catch (const std::bad_alloc&) {
+    return GAL_E_NOMEM;
+  }
+  // five arrays, each starting on a 256-byte boundary (16-byte vector loads)
+  const size_t stride = (sizeof(T) * (size_t)M + 255) & ~size_t(255);
+  void* own = nullptr;
+  int64_t* dperm = nullptr;
+  GAL_CUDA(ctx, cudaMalloc(&own, 5 * stride));
+  cudaError_t e = cudaMalloc(&dperm, sizeof(int64_t) * (size_t)M);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dperm, perm.data(), sizeof(int64_t) * (size_t)M, cudaMemcpyHostToDevice,
+                        st);
+  T* o[5];
+  for (int k = 0; k < 5; ++k) o[k] = reinterpret_cast<T*>(static_cast<char*>(own) + k * stride);
+  const T* in[5] = {u, v, re, im, w};
+  int s = e == cudaSuccess ? GAL_OK : cuda_fail(ctx, e);
+  if (s == GAL_OK)
+    s = stage(ctx, 0, st, [&] { return gal::permute5<T>(dperm, M, in, o, ctx->aux_blocks, st); });
+  if (s == GAL_OK) {
+    e = cudaStreamSynchronize(st);  // the permutation is freed below
+    if (e != cudaSuccess) s = cuda_fail(ctx, e);
+  }
+  if (dperm) cudaFree(dperm);
+  if (s == GAL_OK) s = data_create_t<T>(ctx, o[0], o[1], o[2], o[3], o[4], M, stream, out);
+  if (s != GAL_OK) {
+    cudaFree(own);
+    return s;
+  }
+  (*out)->uv_own = own;
+  return GAL_OK;
+}
 
 template <typename T>
 int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, double dRA,
@@ -1245,6 +1299,16 @@ int gal_data_create_f64(gal_ctx* ctx, const double* u, const double* v, const do
                         const double* im, const double* w, int64_t M, void* stream,
                         gal_data** out) {
   return data_create_t<double>(ctx, u, v, re, im, w, M, stream, out);
+}
+int gal_data_create_sorted_f32(gal_ctx* ctx, const float* u, const float* v, const float* re,
+                               const float* im, const float* w, int64_t M, void* stream,
+                               gal_data** out) {
+  return data_create_sorted_t<float>(ctx, u, v, re, im, w, M, stream, out);
+}
+int gal_data_create_sorted_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
+                               const double* im, const double* w, int64_t M, void* stream,
+                               gal_data** out) {
+  return data_create_sorted_t<double>(ctx, u, v, re, im, w, M, stream, out);
 }
 int gal_data_create_freq_f32(gal_ctx* ctx, const float* u_m, const float* v_m, const float* nu,
                              const float* re, const float* im, const float* w, int64_t M,
