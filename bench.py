@@ -763,10 +763,15 @@ def run_gpu(args):
     if base is not None:
         line["cpu_baseline"] = base
     if world == 1 and not args.no_extras:
-        line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out)
-        line["next"] = measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out)
-        line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
-        line["serving"] = measure_serving(torch, dev)
+        extras = set(args.extras.split(","))
+        if "plane" in extras:
+            line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out)
+        if "next" in extras:
+            line["next"] = measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out)
+        if "batched" in extras:
+            line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
+        if "serving" in extras:
+            line["serving"] = measure_serving(torch, dev)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -783,6 +788,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the beam/full-plane, batched (cube, walkers) and serving "
                          "measurements")
+    ap.add_argument("--extras", default="plane,next,batched,serving",
+                    help="comma-separated extra measurements to run after the bench line "
+                         "(plane, next, batched, serving)")
     ap.add_argument("--variant", default="plain", choices=sorted(VARIANTS),
                     help="options of the timed chi2_image step (plain: the headline line)")
     args = ap.parse_args()
