@@ -48,7 +48,7 @@ extern "C" {
 #define GAL_OK          0
 #define GAL_E_INVAL    -1   /* bad argument: null pointer, nxy not a power of two in [4, 8192],
                                nr < 2, dR <= 0, dxy <= 0, |inc| >= pi/2, M < 0, misaligned array */
-#define GAL_E_NOMEM    -2   /* device allocation failed */
+#define GAL_E_NOMEM    -2   /* device allocation failed, or the context's HBM budget is reached */
 #define GAL_E_CUDA     -3   /* a CUDA runtime call failed */
 #define GAL_E_RANGE    -4   /* internal index check tripped (see gal_check) */
 #define GAL_E_DEVICE   -5   /* no usable CUDA device / wrong architecture */
@@ -91,9 +91,16 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4);
 /* ---- observations ------------------------------------------------------------------- */
 
 /* Device workspace the context holds now (spectra, windows, partial sums,
- * twiddles, staging), in bytes; and the device it was created on. */
+ * twiddles, beam tables, staging images), in bytes; and the device it was
+ * created on. */
 size_t gal_workspace_bytes(const gal_ctx* ctx);
 int gal_device(const gal_ctx* ctx);
+/* Limit the context's workspace (as gal_workspace_bytes counts it) to `bytes`;
+ * 0, the default, sets no limit.  A call that would grow the workspace past
+ * the limit returns GAL_E_NOMEM without evaluating anything (no output is
+ * written), and the workspace already held is kept (lowering the limit frees
+ * nothing; gal_destroy does).  GAL_E_INVAL for a NULL context. */
+int gal_set_hbm_budget(gal_ctx* ctx, size_t bytes);
 
 /* Register an observation of M visibilities: u, v (wavelengths), Re_obs, Im_obs (Jy)
  * and weights w = 1/sigma^2 (Sect. 3.1, Eq. chap6.eq:def.chi.square).  The arrays

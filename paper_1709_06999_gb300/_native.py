@@ -83,6 +83,7 @@ class GalServerStats(ct.Structure):
 
 _SIGNATURES.update({
     "gal_workspace_bytes": (ct.c_size_t, [P]),
+    "gal_set_hbm_budget": (I32, [P, ct.c_size_t]),
     "gal_device": (I32, [P]),
     "gal_data_info": (I32, [P, ct.POINTER(I64), ct.POINTER(I32)]),
     "gal_server_create": (I32, [I32, ct.c_size_t, I32, I32, ct.POINTER(P)]),

@@ -237,6 +237,15 @@ class Context:
             raise ValueError(f"tensor on {t.device}, context on {self.device}")
         return t.contiguous()
 
+    def workspace_bytes(self) -> int:
+        """Device workspace this context holds now (gal_workspace_bytes)."""
+        return int(self.lib.gal_workspace_bytes(self.handle))
+
+    def set_hbm_budget(self, nbytes: int):
+        """Limit this context's workspace to nbytes (0: no limit); a call that
+        would exceed it raises GalError (GAL_E_NOMEM) without evaluating."""
+        _check(self.handle, self.lib.gal_set_hbm_budget(self.handle, int(nbytes)))
+
     def reserve(self, nxy: int, dtype=torch.float32):
         _check(self.handle, self.lib.gal_reserve(self.handle, nxy, 4 if dtype == torch.float32 else 8))
 

@@ -82,6 +82,7 @@ struct gal_ctx {
   uint64_t ws_generation = 0;  // bumped whenever a workspace is reallocated
   bool batch_tuning = true;
   std::map<std::tuple<int, int, int>, gal::BatchShape> batch_shapes;
+  size_t hbm_budget = 0;  // workspace limit in bytes (0: none)
 };
 
 struct gal_data {
@@ -122,8 +123,13 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 // different host threads, e.g. the server's workers)
 std::atomic<uint64_t> g_ws_generation{0};
 
-cudaError_t grow(void** p, size_t* have, size_t need) {
+// Grow one workspace buffer to `need` bytes (contents are not kept).  Growth
+// that would take the context's workspace past its HBM budget fails as an
+// allocation failure would (GAL_E_NOMEM), leaving the buffer as it was.
+cudaError_t grow(gal_ctx* ctx, void** p, size_t* have, size_t need) {
   if (*have >= need) return cudaSuccess;
+  if (ctx->hbm_budget && gal_workspace_bytes(ctx) - *have + need > ctx->hbm_budget)
+    return cudaErrorMemoryAllocation;
   ++g_ws_generation;
   if (*p) {
     cudaError_t e = cudaFree(*p);
@@ -143,8 +149,8 @@ template <typename T> constexpr int prec_index() { return sizeof(T) == 8 ? 1 : 0
 template <typename T> int ensure(gal_ctx* ctx, int nxy, bool full = false) {
   using C = gal::cplx_t<T>;
   const size_t spec = (size_t)nxy * (nxy / 2 + 1) * sizeof(C);
-  GAL_CUDA(ctx, grow(&ctx->F1, &ctx->F1_bytes, full ? (size_t)nxy * nxy * sizeof(C) : spec));
-  GAL_CUDA(ctx, grow(&ctx->Gw, &ctx->Gw_bytes, 2 * spec));  // horizontal node pairs
+  GAL_CUDA(ctx, grow(ctx, &ctx->F1, &ctx->F1_bytes, full ? (size_t)nxy * nxy * sizeof(C) : spec));
+  GAL_CUDA(ctx, grow(ctx, &ctx->Gw, &ctx->Gw_bytes, 2 * spec));  // horizontal node pairs
   const int l = log2i(nxy);
   void*& tw = ctx->tw[prec_index<T>()][l];
   if (!tw) {
@@ -263,7 +269,7 @@ int beam_tables(gal_ctx* ctx, const CallOpts& o, int nxy, double dxy, double dRA
                 double PA, cudaStream_t st, const T** out) {
   *out = nullptr;
   if (!(o.pb_fwhm > 0.0)) return GAL_OK;
-  GAL_CUDA(ctx, grow(&ctx->beam, &ctx->beam_bytes, 2 * (size_t)nxy * sizeof(T)));
+  GAL_CUDA(ctx, grow(ctx, &ctx->beam, &ctx->beam_bytes, 2 * (size_t)nxy * sizeof(T)));
   T* tab = static_cast<T*>(ctx->beam);
   GAL_TRY(stage(ctx, 1, st, [&] {
     return gal::Launch<T>::beam_table(tab, nxy, dxy, o.pb_fwhm, dRA, dDec, PA, st);
@@ -624,7 +630,7 @@ int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, do
   if (!ctx || !image_host || !chi2_host) return GAL_E_INVAL;
   GAL_TRY(check_geometry(nxy, dxy));
   const size_t bytes = (size_t)nxy * nxy * sizeof(T);
-  GAL_CUDA(ctx, grow(&ctx->stage_img, &ctx->stage_img_bytes, bytes));
+  GAL_CUDA(ctx, grow(ctx, &ctx->stage_img, &ctx->stage_img_bytes, bytes));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GAL_CUDA(ctx, cudaMemcpyAsync(ctx->stage_img, image_host, bytes, cudaMemcpyHostToDevice, st));
   GAL_TRY(chi2_image_t<T>(ctx, static_cast<const T*>(ctx->stage_img), nxy, dxy, dRA, dDec, PA, d,
@@ -664,7 +670,7 @@ int chi2_image_host_async_t(gal_ctx* ctx, const T* image_host, int nxy, double d
   const size_t bytes = (size_t)nxy * nxy * sizeof(T);
   if (ctx->pipe_img_bytes[s] < bytes) {  // regrow only once the buffer's last use is done
     GAL_CUDA(ctx, cudaEventSynchronize(ctx->pipe_done[s]));
-    GAL_CUDA(ctx, grow(&ctx->pipe_img[s], &ctx->pipe_img_bytes[s], bytes));
+    GAL_CUDA(ctx, grow(ctx, &ctx->pipe_img[s], &ctx->pipe_img_bytes[s], bytes));
   }
   GAL_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pipe_done[s], 0));
   GAL_CUDA(ctx, cudaMemcpyAsync(ctx->pipe_img[s], image_host, bytes, cudaMemcpyHostToDevice,
@@ -833,10 +839,10 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
     offs[p].push_back(o);
     pl.max_nxy[p] = std::max(pl.max_nxy[p], r.nxy);
   }
-  GAL_CUDA(ctx, grow(&ctx->batch_ws, &ctx->batch_ws_bytes, bytes));
+  GAL_CUDA(ctx, grow(ctx, &ctx->batch_ws, &ctx->batch_ws_bytes, bytes));
   if (nctr > ctx->batch_ctr_n) {
     size_t have = ctx->batch_ctr_n * sizeof(unsigned);
-    GAL_CUDA(ctx, grow(reinterpret_cast<void**>(&ctx->batch_ctr), &have, nctr * sizeof(unsigned)));
+    GAL_CUDA(ctx, grow(ctx, reinterpret_cast<void**>(&ctx->batch_ctr), &have, nctr * sizeof(unsigned)));
     GAL_CUDA(ctx, cudaMemset(ctx->batch_ctr, 0, nctr * sizeof(unsigned)));
     ctx->batch_ctr_n = nctr;
   }
@@ -1198,7 +1204,9 @@ int gal_stage_times(gal_ctx* ctx, double* ms_out4, int64_t* count_out4) {
 size_t gal_workspace_bytes(const gal_ctx* ctx) {
   if (!ctx) return 0;
   size_t b = ctx->F1_bytes + ctx->Gw_bytes + ctx->batch_ws_bytes + ctx->stage_img_bytes +
-             ctx->batch_ctr_n * sizeof(unsigned) + sizeof(double) * (size_t)ctx->partials_len;
+             ctx->batch_ctr_n * sizeof(unsigned) + sizeof(double) * (size_t)ctx->partials_len +
+             ctx->beam_bytes + ctx->pipe_img_bytes[0] + ctx->pipe_img_bytes[1] +
+             (ctx->pipe_chi2 ? 2 * sizeof(double) : 0);
   for (int p = 0; p < 2; ++p)
     for (int l = 0; l <= kMaxLog2; ++l)
       if (ctx->tw[p][l]) b += ((size_t)1 << l) * (p ? 16 : 8);
@@ -1206,6 +1214,12 @@ size_t gal_workspace_bytes(const gal_ctx* ctx) {
 }
 
 int gal_device(const gal_ctx* ctx) { return ctx ? ctx->device : -1; }
+
+int gal_set_hbm_budget(gal_ctx* ctx, size_t bytes) {
+  if (!ctx) return GAL_E_INVAL;
+  ctx->hbm_budget = bytes;
+  return GAL_OK;
+}
 
 int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, void* stream) {
   if (!ctx || n < 0 || (n > 0 && (!reqs || !chi2_out))) return GAL_E_INVAL;

@@ -332,6 +332,30 @@ def test_workspace_regrowth_and_counters(ctx):
     assert all(ms > 0 for ms, n in times if n)
 
 
+def test_hbm_budget():
+    """A context's workspace limit: growth past it is GAL_E_NOMEM with the
+    workspace unchanged and nothing evaluated; calls within it still run."""
+    from paper_1709_06999_gb300 import Context, GalError
+    s = synth()
+    c = Context(0)
+    p = s.small_image_problem(nxy=64, M=2001, seed=3)
+    obs = c.register(*(dev(a, torch.float32) for a in (p.u, p.v, p.noise_re, p.noise_im, p.w)))
+    small = dev(p.image, torch.float32)
+    a = c.chi2_image(small, p.dxy, obs).item()
+    held = c.workspace_bytes()
+    c.set_hbm_budget(held)
+    assert c.chi2_image(small, p.dxy, obs).item() == a  # no growth needed
+    big = torch.zeros(1024, 1024, dtype=torch.float32, device="cuda")
+    out = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(GalError, match="status -2"):
+        c.chi2_image(big, p.dxy, obs, out=out)
+    assert out.item() == -1.0 and c.workspace_bytes() == held
+    c.set_hbm_budget(0)
+    c.chi2_image(big, p.dxy, obs, out=out)
+    assert out.item() != -1.0 and c.workspace_bytes() > held
+    c.close()
+
+
 # ----------------------------------------------------------------------------
 # full size, in the benchmark's launch configuration (registered observation,
 # chi2_image; float32 is the bench line, float64 its plain FP64 comparison):
