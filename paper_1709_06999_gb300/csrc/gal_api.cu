@@ -278,6 +278,15 @@ int beam_tables(gal_ctx* ctx, const CallOpts& o, int nxy, double dxy, double dRA
   return GAL_OK;
 }
 
+// Everything a call of side nxy may grow, grown before it enqueues anything,
+// so that a failed allocation (or the HBM budget) leaves nothing enqueued.
+template <typename T> int reserve_call(gal_ctx* ctx, int nxy, const CallOpts& o) {
+  GAL_TRY(ensure<T>(ctx, nxy, o.full));
+  if (o.pb_fwhm > 0.0)
+    GAL_CUDA(ctx, grow(ctx, &ctx->beam, &ctx->beam_bytes, 2 * (size_t)nxy * sizeof(T)));
+  return GAL_OK;
+}
+
 // FFT of the image (or of the swept profile) into the pruned window ctx->Gw;
 // `beam` multiplies the pixels (null: none), `full` keeps both signs of u.
 template <typename T>
@@ -310,6 +319,7 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   if (!u || !v || !vis) return GAL_E_INVAL;
   if (!aligned(u, sizeof(T)) || !aligned(v, sizeof(T)) || !aligned(vis, 2 * sizeof(T)))
     return GAL_E_INVAL;
+  GAL_TRY(reserve_call<T>(ctx, nxy, o));
   GAL_TRY(stage(ctx, 0, st, [&] {
     return gal::Launch<T>::extent(u, v, M, ctx->rho2, ctx->aux_blocks, st);
   }));
@@ -369,6 +379,7 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
     return GAL_OK;
   }
   using C = gal::cplx_t<T>;
+  GAL_TRY(reserve_call<T>(ctx, nxy, o));
   const gal::Bounds bd = gal::make_bounds(d->rho2_host, (double)nxy * dxy, nxy);
   const T* beam;
   GAL_TRY(beam_tables<T>(ctx, o, nxy, dxy, dRA, dDec, PA, st, &beam));
@@ -631,6 +642,7 @@ int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, do
   GAL_TRY(check_geometry(nxy, dxy));
   const size_t bytes = (size_t)nxy * nxy * sizeof(T);
   GAL_CUDA(ctx, grow(ctx, &ctx->stage_img, &ctx->stage_img_bytes, bytes));
+  GAL_TRY(reserve_call<T>(ctx, nxy, CallOpts{}));  // before the copy is enqueued
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   GAL_CUDA(ctx, cudaMemcpyAsync(ctx->stage_img, image_host, bytes, cudaMemcpyHostToDevice, st));
   GAL_TRY(chi2_image_t<T>(ctx, static_cast<const T*>(ctx->stage_img), nxy, dxy, dRA, dDec, PA, d,
@@ -672,6 +684,7 @@ int chi2_image_host_async_t(gal_ctx* ctx, const T* image_host, int nxy, double d
     GAL_CUDA(ctx, cudaEventSynchronize(ctx->pipe_done[s]));
     GAL_CUDA(ctx, grow(ctx, &ctx->pipe_img[s], &ctx->pipe_img_bytes[s], bytes));
   }
+  GAL_TRY(reserve_call<T>(ctx, nxy, CallOpts{}));  // before the copy is enqueued
   GAL_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pipe_done[s], 0));
   GAL_CUDA(ctx, cudaMemcpyAsync(ctx->pipe_img[s], image_host, bytes, cudaMemcpyHostToDevice,
                                 ctx->copy_stream));

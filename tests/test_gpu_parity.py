@@ -347,9 +347,17 @@ def test_hbm_budget():
     assert c.chi2_image(small, p.dxy, obs).item() == a  # no growth needed
     big = torch.zeros(1024, 1024, dtype=torch.float32, device="cuda")
     out = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    u, v = dev(p.u, torch.float32), dev(p.v, torch.float32)
+    vis = torch.full((u.numel(), 2), -1.0, dtype=torch.float32, device="cuda")
+    launches = c.launch_count()
     with pytest.raises(GalError, match="status -2"):
         c.chi2_image(big, p.dxy, obs, out=out)
-    assert out.item() == -1.0 and c.workspace_bytes() == held
+    with pytest.raises(GalError, match="status -2"):
+        c.chi2_image(big, p.dxy, obs, out=out, pb_fwhm=1e-4)
+    with pytest.raises(GalError, match="status -2"):
+        c.sample_image(big, p.dxy, u, v, out=vis)
+    assert c.launch_count() == launches  # nothing was enqueued
+    assert out.item() == -1.0 and bool((vis == -1.0).all()) and c.workspace_bytes() == held
     c.set_hbm_budget(0)
     c.chi2_image(big, p.dxy, obs, out=out)
     assert out.item() != -1.0 and c.workspace_bytes() > held
