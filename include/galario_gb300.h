@@ -135,6 +135,12 @@ int gal_data_create_sorted_f32(gal_ctx* ctx, const float* u, const float* v, con
 int gal_data_create_sorted_f64(gal_ctx* ctx, const double* u, const double* v, const double* re,
                                const double* im, const double* w, int64_t M, void* stream,
                                gal_data** out);
+/* The order gal_data_create_sorted_* stores an observation in, computed on the
+ * host from host arrays u, v: perm_out[i] (M values, caller-owned) is the input
+ * index of the i-th stored point.  No device work.  GAL_E_INVAL for M < 0 or a
+ * null pointer with M > 0; GAL_E_NOMEM if the host buffers cannot be had. */
+int gal_z_order_f32(const float* u, const float* v, int64_t M, int64_t* perm_out);
+int gal_z_order_f64(const double* u, const double* v, int64_t M, int64_t* perm_out);
 /* Register an observation whose baselines u_m, v_m are in metres, with the
  * frequency nu (Hz) of every visibility (lifts the single-frequency assumption
  * of Sect. 3: each visibility samples the model at its own u_m nu / c).  The

@@ -32,6 +32,7 @@ for _p in ("f32", "f64"):
         f"gal_data_create_{_p}": (I32, [P, P, P, P, P, P, I64, P, ct.POINTER(P)]),
         f"gal_data_create_freq_{_p}": (I32, [P, P, P, P, P, P, P, I64, P, ct.POINTER(P)]),
         f"gal_data_create_sorted_{_p}": (I32, [P, P, P, P, P, P, I64, P, ct.POINTER(P)]),
+        f"gal_z_order_{_p}": (I32, [P, P, I64, P]),
         f"gal_sweep_{_p}": (I32, [P, P, I32, D, D, I32, D, D, P, P]),
         f"gal_sample_image_{_p}": (I32, [P, P, I32, D, D, D, D, I64, P, P, P, P]),
         f"gal_sample_profile_{_p}": (I32, [P, P, I32, D, D, I32, D, D, D, D, D, I64, P, P, P, P]),

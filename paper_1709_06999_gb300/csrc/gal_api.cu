@@ -635,6 +635,19 @@ int data_create_sorted_t(gal_ctx* ctx, const T* u, const T* v, const T* re, cons
   return GAL_OK;
 }
 
+// The Z-order of host arrays u, v into perm_out (gal_z_order_*).
+template <typename T> int z_order_t(const T* u, const T* v, int64_t M, int64_t* perm_out) {
+  if (M < 0 || (M > 0 && (!u || !v || !perm_out))) return GAL_E_INVAL;
+  try {
+    std::vector<int64_t> perm;
+    gal::z_order<T>(u, v, M, perm);
+    if (M > 0) std::memcpy(perm_out, perm.data(), sizeof(int64_t) * (size_t)M);
+  } catch (const std::bad_alloc&) {
+    return GAL_E_NOMEM;
+  }
+  return GAL_OK;
+}
+
 template <typename T>
 int chi2_image_host_t(gal_ctx* ctx, const T* image_host, int nxy, double dxy, double dRA,
                       double dDec, double PA, const gal_data* d, double* chi2_host, void* stream) {
@@ -1336,6 +1349,12 @@ int gal_data_create_sorted_f64(gal_ctx* ctx, const double* u, const double* v, c
                                const double* im, const double* w, int64_t M, void* stream,
                                gal_data** out) {
   return data_create_sorted_t<double>(ctx, u, v, re, im, w, M, stream, out);
+}
+int gal_z_order_f32(const float* u, const float* v, int64_t M, int64_t* perm_out) {
+  return z_order_t<float>(u, v, M, perm_out);
+}
+int gal_z_order_f64(const double* u, const double* v, int64_t M, int64_t* perm_out) {
+  return z_order_t<double>(u, v, M, perm_out);
 }
 int gal_data_create_freq_f32(gal_ctx* ctx, const float* u_m, const float* v_m, const float* nu,
                              const float* re, const float* im, const float* w, int64_t M,
