@@ -197,7 +197,7 @@ cudaError_t BatchLaunch<T>::beams(const BatchItem* it, int n, int* launches, cud
       jb.j[k] = BeamJob<T>{static_cast<T*>(b.beam), b.N, b.sp.dxy, b.bp.c, b.bp.bx, b.bp.by};
       nmax = b.N > nmax ? b.N : nmax;
     }
-    beam_tables_kernel<T, kBatchJobs><<<dim3((2 * nmax + 255) / 256, m), 256, 0, st>>>(jb);
+    beam_tables_kernel<T, kBatchJobs><<<dim3((2 * nmax + 63) / 64, m), 64, 0, st>>>(jb);
     const cudaError_t e = cudaGetLastError();
     if (!e) ++*launches;
     return e;

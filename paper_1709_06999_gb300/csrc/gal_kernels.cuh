@@ -1731,7 +1731,9 @@ template <typename T>
 cudaError_t Launch<T>::beam_table(T* tab, int N, double dxy, double fwhm, double dRA, double dDec,
                                   double PA, cudaStream_t st) {
   const BeamParams b = beam_params(fwhm, dRA, dDec, PA);
-  beam_table_kernel<T><<<(2 * N + 255) / 256, 256, 0, st>>>(tab, N, dxy, b.c, b.bx, b.by);
+  // small blocks spread the 2N FP64 exponentials over many SMs: the FP64
+  // pipe of one SM, not the launch, bounds this kernel
+  beam_table_kernel<T><<<(2 * N + 63) / 64, 64, 0, st>>>(tab, N, dxy, b.c, b.bx, b.by);
   return cudaGetLastError();
 }
 
