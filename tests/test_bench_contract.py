@@ -1,0 +1,55 @@
+"""bench.py on the CPU: the reference arm's JSON line (the FP64 oracle timed
+on the host) and the host-side helpers behind the native line's roofline.
+No GPU needed."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_line():
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    line = json.loads(p.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 1 and line["warmup"] == 3
+    assert line["unit"] == "evals/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "evals/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["nxy"] == 4096 and line["config"]["M"] == 5_000_000
+
+
+def test_window_rule():
+    # e = rho * S cells: k = floor(e) + 3 cells of margin, Kc = k + 1 columns
+    # and rows N/2 - k .. N/2 + k, clipped to the half spectrum
+    assert bench.window(57.5, 1.0, 4096) == (61, 121)
+    assert bench.window(0.0, 1.0, 64) == (4, 7)
+    assert bench.window(100.0, 1.0, 64) == (33, 64)        # whole half spectrum
+    assert bench.window(31.0, 1.0, 64) == (33, 64)         # margins clipped
+    assert bench.window(float("nan"), 1.0, 64) == (33, 64)
+
+
+def test_full_window_columns():
+    assert bench.full_window_columns(61, 4096) == 121       # u from -60 to 60
+    assert bench.full_window_columns(33, 64) == 64          # node range -32 .. 31
+    assert bench.full_window_columns(2, 64) == 3
+
+
+def test_algorithmic_bytes():
+    N, M, Kc, nrw = 4096, 5_000_000, 61, 121
+    assert bench.algorithmic_bytes(1, N, M, Kc, nrw) == 4 * N * N + 8 * N * Kc
+    assert bench.algorithmic_bytes(1, N, M, Kc, nrw, beam=True) == 4 * N * N + 8 * N * Kc + 8 * N
+    assert bench.algorithmic_bytes(2, N, M, Kc, nrw) == 8 * N * Kc + 8 * nrw * Kc
+    # the headline gather: 20 B per point plus the window once
+    assert bench.algorithmic_bytes(3, N, M, Kc, nrw) == 100_059_048
