@@ -429,6 +429,14 @@ int gal_server_add_data_f32(gal_server* s, const float* u, const float* v, const
                             const float* im, const float* w, int64_t M, gal_data** out);
 int gal_server_add_data_f64(gal_server* s, const double* u, const double* v, const double* re,
                             const double* im, const double* w, int64_t M, gal_data** out);
+/* As gal_server_add_data_*, registered in Z-order as gal_data_create_sorted_*
+ * does (the server keeps its own copies; the arrays may be freed after the
+ * call, which synchronises the device).  Same budget charge and errors. */
+int gal_server_add_data_sorted_f32(gal_server* s, const float* u, const float* v, const float* re,
+                                   const float* im, const float* w, int64_t M, gal_data** out);
+int gal_server_add_data_sorted_f64(gal_server* s, const double* u, const double* v,
+                                   const double* re, const double* im, const double* w, int64_t M,
+                                   gal_data** out);
 /* Queue one request (copied); *ticket identifies it.  GAL_E_INVAL for an invalid
  * request, GAL_E_BUSY when 65536 requests are already waiting. */
 int gal_server_submit(gal_server* s, const gal_request* req, uint64_t* ticket);

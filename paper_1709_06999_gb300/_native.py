@@ -90,6 +90,8 @@ _SIGNATURES.update({
     "gal_server_create": (I32, [I32, ct.c_size_t, I32, I32, ct.POINTER(P)]),
     "gal_server_add_data_f32": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
     "gal_server_add_data_f64": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
+    "gal_server_add_data_sorted_f32": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
+    "gal_server_add_data_sorted_f64": (I32, [P, P, P, P, P, P, I64, ct.POINTER(P)]),
     "gal_server_submit": (I32, [P, ct.POINTER(GalRequest), ct.POINTER(ct.c_uint64)]),
     "gal_server_submit_many": (I32, [P, ct.POINTER(GalRequest), I32, ct.POINTER(ct.c_uint64)]),
     "gal_server_wait": (I32, [P, ct.c_uint64, I32, ct.POINTER(D), ct.POINTER(D)]),

@@ -484,12 +484,13 @@ class Context:
 
 
 class ServedData:
-    """An observation held by a Server (borrowed tensors kept alive here)."""
+    """An observation held by a Server (borrowed tensors kept alive here;
+    none when the server keeps its own copies)."""
 
-    def __init__(self, handle, tensors):
+    def __init__(self, handle, tensors, dtype):
         self.handle = handle
         self._tensors = tensors
-        self.dtype = tensors[0].dtype
+        self.dtype = dtype
 
 
 class Server:
@@ -508,16 +509,19 @@ class Server:
         self._data = []
         self._inflight = {}
 
-    def add_data(self, u, v, re, im, w) -> ServedData:
+    def add_data(self, u, v, re, im, w, z_order: bool = False) -> ServedData:
+        """Register an observation for requests (charged to the budget);
+        z_order=True keeps library copies ordered along the uv plane."""
         tensors = [t.to(self.device).contiguous() for t in (u, v, re, im, w)]
         m = tensors[0].numel()
         if any(t.numel() != m for t in tensors):
             raise ValueError("u, v, re, im, w must have the same length")
         sfx = _suffix(*tensors)
         h = ct.c_void_p()
-        fn = getattr(self.lib, f"gal_server_add_data_{sfx}")
+        name = f"gal_server_add_data_sorted_{sfx}" if z_order else f"gal_server_add_data_{sfx}"
+        fn = getattr(self.lib, name)
         _check(None, fn(self.handle, *[t.data_ptr() for t in tensors], m, ct.byref(h)))
-        d = ServedData(ct.c_void_p(h.value), tensors)
+        d = ServedData(ct.c_void_p(h.value), [] if z_order else tensors, tensors[0].dtype)
         self._data.append(d)
         return d
 

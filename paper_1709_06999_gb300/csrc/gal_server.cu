@@ -293,7 +293,7 @@ int gal_server_create(int device, size_t hbm_budget_bytes, int slots, int max_ba
 }
 
 static int add_data(gal_server* s, const void* u, const void* v, const void* re, const void* im,
-                    const void* w, int64_t M, int rb, gal_data** out) {
+                    const void* w, int64_t M, int rb, bool z_order, gal_data** out) {
   if (!s || !out || M < 0) return GAL_E_INVAL;
   const size_t bytes = 5 * (size_t)M * (size_t)rb;
   {
@@ -301,16 +301,17 @@ static int add_data(gal_server* s, const void* u, const void* v, const void* re,
     if (s->data_bytes + bytes > s->budget) return GAL_E_NOMEM;
   }
   cudaSetDevice(s->device);
+  // z_order: the library keeps its own copies (the budget charges the same
+  // 5 M values either way)
+  auto f32 = z_order ? gal_data_create_sorted_f32 : gal_data_create_f32;
+  auto f64 = z_order ? gal_data_create_sorted_f64 : gal_data_create_f64;
   const int st =
-      rb == 4 ? gal_data_create_f32(s->primary, static_cast<const float*>(u),
-                                    static_cast<const float*>(v), static_cast<const float*>(re),
-                                    static_cast<const float*>(im), static_cast<const float*>(w),
-                                    M, nullptr, out)
-              : gal_data_create_f64(s->primary, static_cast<const double*>(u),
-                                    static_cast<const double*>(v),
-                                    static_cast<const double*>(re),
-                                    static_cast<const double*>(im),
-                                    static_cast<const double*>(w), M, nullptr, out);
+      rb == 4 ? f32(s->primary, static_cast<const float*>(u), static_cast<const float*>(v),
+                    static_cast<const float*>(re), static_cast<const float*>(im),
+                    static_cast<const float*>(w), M, nullptr, out)
+              : f64(s->primary, static_cast<const double*>(u), static_cast<const double*>(v),
+                    static_cast<const double*>(re), static_cast<const double*>(im),
+                    static_cast<const double*>(w), M, nullptr, out);
   if (st != GAL_OK) return st;
   std::lock_guard<std::mutex> lk(s->mu);
   s->data.push_back(*out);
@@ -320,11 +321,20 @@ static int add_data(gal_server* s, const void* u, const void* v, const void* re,
 
 int gal_server_add_data_f32(gal_server* s, const float* u, const float* v, const float* re,
                             const float* im, const float* w, int64_t M, gal_data** out) {
-  return add_data(s, u, v, re, im, w, M, 4, out);
+  return add_data(s, u, v, re, im, w, M, 4, false, out);
 }
 int gal_server_add_data_f64(gal_server* s, const double* u, const double* v, const double* re,
                             const double* im, const double* w, int64_t M, gal_data** out) {
-  return add_data(s, u, v, re, im, w, M, 8, out);
+  return add_data(s, u, v, re, im, w, M, 8, false, out);
+}
+int gal_server_add_data_sorted_f32(gal_server* s, const float* u, const float* v, const float* re,
+                                   const float* im, const float* w, int64_t M, gal_data** out) {
+  return add_data(s, u, v, re, im, w, M, 4, true, out);
+}
+int gal_server_add_data_sorted_f64(gal_server* s, const double* u, const double* v,
+                                   const double* re, const double* im, const double* w, int64_t M,
+                                   gal_data** out) {
+  return add_data(s, u, v, re, im, w, M, 8, true, out);
 }
 
 static int make_pending(const gal_request* req, Pending* p) {

@@ -82,6 +82,42 @@ def test_alone_equals_mix(dt):
     srv.close()
 
 
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_z_order_data(dt):
+    """An observation added in Z-order: served alone and in a burst bitwise
+    equal, bitwise equal to single calls on a Z-order registration of the
+    same arrays, and equal up to summation rounding to the input order."""
+    srv = Server(0, hbm_budget=8 * 10**9, slots=4, max_batch=8)
+    rng = np.random.default_rng(5)
+    m = 40_001
+    u, v = synth.uv_loguniform(m, 1e4, 3e6, rng)
+    w = synth.weights_uniform(m, rng)
+    nre, nim = synth.noise(w, rng)
+    arrs = [dev(a, dt) for a in (u, v, nre, nim, w)]
+    plain = srv.add_data(*arrs)
+    zo = srv.add_data(*arrs, z_order=True)
+    reqs_p = requests([plain], dt, 12, seed=3)
+    reqs_z = requests([zo], dt, 12, seed=3)   # the same geometries and models
+    alone = [srv.wait(srv.submit(r))[0] for r in reqs_z]
+    mix = [srv.wait(t)[0] for t in srv.submit_many(reqs_z)]
+    assert mix == alone
+    ctx = Context(0)
+    obs = ctx.register(*arrs, z_order=True)
+    single_z = []
+    for r in reqs_z:
+        if r.image is not None:
+            single_z.append(ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA).item())
+        else:
+            single_z.append(ctx.chi2_profile(r.intensity, r.Rmin, r.dR, r.nxy, r.dxy, obs, r.inc,
+                                             r.dRA, r.dDec, r.PA).item())
+    assert single_z == alone
+    tol = 1e-6 if dt == torch.float32 else 1e-12
+    in_order = [srv.wait(srv.submit(r))[0] for r in reqs_p]
+    for a, b in zip(alone, in_order):
+        assert abs(a - b) <= tol * abs(b)
+    srv.close()
+
+
 def test_beams_alone_equal_mix():
     """Requests with per-request primary beams and some on the full-plane
     spectrum, served alone and in a burst: bitwise equal to each other and to
