@@ -870,6 +870,9 @@ int plan_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, B
     size_t have = ctx->batch_ctr_n * sizeof(unsigned);
     GAL_CUDA(ctx, grow(ctx, reinterpret_cast<void**>(&ctx->batch_ctr), &have, nctr * sizeof(unsigned)));
     GAL_CUDA(ctx, cudaMemset(ctx->batch_ctr, 0, nctr * sizeof(unsigned)));
+    // the memset runs on the legacy stream, which a non-blocking stream does
+    // not wait for: finish it before any launch reads the counters
+    GAL_CUDA(ctx, cudaStreamSynchronize(0));
     ctx->batch_ctr_n = nctr;
   }
   char* base = static_cast<char*>(ctx->batch_ws);
@@ -1201,6 +1204,7 @@ int gal_check(gal_ctx* ctx) {
   int flag = 0;
   GAL_CUDA(ctx, cudaMemcpy(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost));
   GAL_CUDA(ctx, cudaMemset(ctx->err, 0, sizeof(int)));
+  GAL_CUDA(ctx, cudaStreamSynchronize(0));  // cleared before any later launch
   return flag ? GAL_E_RANGE : GAL_OK;
 }
 
