@@ -26,6 +26,9 @@
  *   stream).  Entry points only enqueue work; they do not synchronise unless
  *   documented (the `_host` variants do).  A context must be used by one host
  *   thread and one stream at a time: its workspace is shared by its calls.
+ * Device: work is enqueued on the calling thread's current CUDA device, which
+ *   must be the context's (gal_create makes it current); a stream of another
+ *   device makes the launch fail with GAL_E_CUDA.
  * Errors: every int-returning call returns GAL_OK (0) or a negative GAL_E_*
  *   code; gal_strerror() names it.  On error nothing has been enqueued, except
  *   for GAL_E_CUDA, which reports a failed CUDA call (the message of the last

@@ -228,6 +228,10 @@ class Context:
             pass
 
     def _stream(self) -> int:
+        # the library enqueues on the calling thread's current device
+        if torch.cuda.current_device() != self.device.index:
+            raise GalError(f"current CUDA device is {torch.cuda.current_device()}, the context's "
+                           f"is {self.device.index}: select it first (torch.cuda.set_device)")
         return torch.cuda.current_stream(self.device).cuda_stream
 
     def _dev(self, t):
