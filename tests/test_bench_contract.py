@@ -53,3 +53,13 @@ def test_algorithmic_bytes():
     assert bench.algorithmic_bytes(2, N, M, Kc, nrw) == 8 * N * Kc + 8 * nrw * Kc
     # the headline gather: 20 B per point plus the window once
     assert bench.algorithmic_bytes(3, N, M, Kc, nrw) == 100_059_048
+
+
+def test_cpu_baseline_fields(monkeypatch):
+    import time
+    monkeypatch.setattr(bench, "oracle_eval", lambda p, re, im: time.sleep(0.01))
+    b = bench.cpu_baseline(None, None, None, 3)
+    assert b["kind"] == "oracle" and b["cores"] == 1 and b["unit"] == "evals/s"
+    s = b["seconds_per_eval"]
+    assert 0.009 < s["min"] <= s["median"] < 1.0
+    assert 1.0 < b["value"] <= 1.0 / s["min"]
