@@ -83,6 +83,17 @@ def window(rho: float, S: float, N: int):
     return min(k + 1, P), hi - lo + 1
 
 
+def fft_equivalent(nxy: int, evals_per_s: float) -> dict:
+    """Secondary figure: the nominal flop count of an unpruned real-to-complex
+    2D FFT of the image, 2.5 N^2 log2(N^2), per evaluation and at the measured
+    rate.  The pruned transform executes fewer flops; this is the customary
+    FFT-equivalent rate, not a count of executed instructions."""
+    gflop = 2.5 * nxy * nxy * math.log2(float(nxy) * nxy) / 1e9
+    return {"fft_gflop_per_eval": gflop, "fft_equivalent_tflop_per_s": gflop * evals_per_s / 1e3,
+            "note": "nominal 2.5 N^2 log2(N^2) of an unpruned R2C 2D FFT; the pruned "
+                    "transform executes fewer"}
+
+
 def full_window_columns(Kc: int, N: int) -> int:
     """Columns of the full-plane window (same rule as the library): u from
     -(Kc-1) to Kc-1 when pruned, the node range -N/2 .. N/2-1 otherwise."""
@@ -761,6 +772,7 @@ def run_gpu(args):
                        "tenth step",
         "fp64_plain": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
                        "note": "same workload through the float64 entry point, single calls"},
+        "flops": fft_equivalent(NXY, value),
         "clocks": clk.summary(),
     }
     if base is not None:

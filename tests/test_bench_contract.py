@@ -63,3 +63,9 @@ def test_cpu_baseline_fields(monkeypatch):
     s = b["seconds_per_eval"]
     assert 0.009 < s["min"] <= s["median"] < 1.0
     assert 1.0 < b["value"] <= 1.0 / s["min"]
+
+
+def test_fft_equivalent():
+    f = bench.fft_equivalent(4096, 1000.0)
+    assert abs(f["fft_gflop_per_eval"] - 2.5 * 4096 ** 2 * 24 / 1e9) < 1e-12
+    assert abs(f["fft_equivalent_tflop_per_s"] - f["fft_gflop_per_eval"]) < 1e-12
