@@ -367,7 +367,10 @@ typedef struct gal_request {
  * the whole batch costs about three launches per distinct image side instead
  * of three per request.  Every result is bitwise equal to the corresponding
  * single call on the same context (same kernels, block partitions and
- * reduction trees).  Requests the batched kernels do not cover (nxy < 32 in
+ * reduction trees: a batched gather runs each request's single-call blocks as
+ * virtual blocks, several to a launched block, so the request's spectrum
+ * window is copied into shared memory fewer times).  Requests the batched
+ * kernels do not cover (nxy < 32 in
  * float32 / < 16 in float64, nxy above 8192 / 4096, images not 16-byte
  * aligned) run as single calls inside the batch.
  * Launch shapes: the first batch of each (precision, request count, largest
