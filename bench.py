@@ -142,57 +142,145 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# NVML clock-event reason bits (nvml.h, nvmlClocksEventReason*): the ones the
+# timing rules name, plus idle
+NVML_REASONS = {0x1: "gpu_idle", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+                0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+                0x80: "hw_power_brake_slowdown"}
+
+
+def nvml_sample_loop(target: str, period_s: float, out=None) -> int:
+    """Child process of ClockSampler: read-only NVML queries of one GPU (SM
+    clock, its maximum, power and the clock-event reasons) every period_s
+    seconds, one line per sample: "unix_time sm_mhz max_mhz power_w reasons".
+    target is "pci:<bus id>", "uuid:<GPU-...>" or "index:<n>".  Runs until
+    killed."""
+    import ctypes
+    out = out or sys.stdout
+    try:
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+    except OSError:
+        return 1
+    if lib.nvmlInit_v2() != 0:
+        return 1
+    h = ctypes.c_void_p()
+    kind, _, val = target.partition(":")
+    if kind == "pci":
+        rc = lib.nvmlDeviceGetHandleByPciBusId_v2(val.encode(), ctypes.byref(h))
+    elif kind == "uuid":
+        rc = lib.nvmlDeviceGetHandleByUUID(val.encode(), ctypes.byref(h))
+    else:
+        rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(int(val)), ctypes.byref(h))
+    if rc != 0:
+        return 1
+    reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+        lib.nvmlDeviceGetCurrentClocksThrottleReasons
+    sm, mx, mw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx))  # NVML_CLOCK_SM = 1
+    while True:
+        lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(sm))
+        lib.nvmlDeviceGetPowerUsage(h, ctypes.byref(mw))
+        reasons_fn(h, ctypes.byref(rs))
+        out.write(f"{time.time():.6f} {sm.value} {mx.value} {mw.value / 1000.0:.1f} "
+                  f"{rs.value}\n")
+        out.flush()
+        time.sleep(period_s)
+
+
+def parse_clock_samples(lines, t0: float, t1: float):
+    """Summary of sampler lines for the window [t0, t1] (unix seconds).  When
+    the window is shorter than the sampling period and holds no sample, the
+    last sample before it and the first after it stand for it (said so in
+    "window")."""
+    rows = []
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) != 5:
+            continue
+        try:
+            rows.append((float(parts[0]), float(parts[1]), float(parts[2]), float(parts[3]),
+                         int(parts[4])))
+        except ValueError:
+            continue
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"],
+                "note": "no NVML sample was read"}
+    inside = [r for r in rows if t0 <= r[0] <= t1]
+    window = "timed region"
+    if not inside:
+        before = [r for r in rows if r[0] < t0][-1:]
+        after = [r for r in rows if r[0] > t1][:1]
+        inside = before + after
+        window = "nearest samples before and after the timed region (shorter than the period)"
+    reasons = set()
+    for r in inside:
+        for bit, name in NVML_REASONS.items():
+            if r[4] & bit and name != "gpu_idle":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(r[1] for r in inside),
+            "sm_max_mhz": max(r[2] for r in inside),
+            "power_w_max": max(r[3] for r in inside),
+            "reasons": sorted(reasons), "samples": len(inside), "window": window,
+            "source": "NVML, read-only queries"}
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    """SM clock, power and clock-event reasons of the bench's GPU, sampled by a
+    child process every 0.5 ms through NVML (read-only queries).  Start it
+    before the warm-up (the child needs a moment to come up); mark() records
+    the timed region, summary() reports the samples inside it."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, device_index: int, period_s: float = 0.0005):
+        self.device_index = device_index
+        self.period = period_s
         self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
 
-    def __enter__(self):
+    def _target(self):
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(self.device_index)
+            if hasattr(pr, "pci_bus_id"):
+                return f"pci:{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            return f"uuid:GPU-{pr.uuid}"
+        except Exception:  # pragma: no cover - sampler is best effort
+            return f"index:{self.device_index}"
+
+    def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                [sys.executable, os.path.abspath(__file__), "--clock-sampler", self._target(),
+                 str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            # wait (at most 20 s) for the first sample, so the timed region is covered
+            import select
+            if select.select([self.proc.stdout], [], [], 20.0)[0]:
+                line = self.proc.stdout.readline()
+                if line:
+                    self.lines.append(line)
         except OSError:
             self.proc = None
         return self
 
-    def __exit__(self, *exc):
-        self.lines = []
-        if self.proc is not None:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return
+        time.sleep(3 * self.period)  # one sample after the region
+        self.proc.kill()
+        out, _ = self.proc.communicate()
+        self.lines += out.splitlines()
+        self.proc = None
 
     def summary(self):
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        if not sm:
+        if self.t0 is None or self.t1 is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_samples(self.lines, self.t0, self.t1)
 
 
 def dist_setup():
@@ -205,6 +293,34 @@ def dist_setup():
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
+def host_info() -> dict:
+    """The host CPU: model name (lscpu, else /proc/cpuinfo), logical CPUs, and
+    the CPUs this process may run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model, "nproc": os.cpu_count(), "usable_cpus": usable}
+
+
 def oracle_eval(p, re, im):
     import oracle
     return oracle.chi2_image(p.image, p.dxy, p.u, p.v, re, im, p.w, p.dRA, p.dDec, p.PA)
@@ -219,30 +335,74 @@ def make_problem(seed: int = 2):
     return p
 
 
+def oracle_eval_threads(p, re, im, pool, nthreads: int):
+    """One full oracle evaluation on all host cores: the oracle's own image FFT
+    (one call), then its sampling and chi-square on nthreads contiguous shares
+    of the points in a thread pool (numpy releases the GIL in its array loops),
+    the shares' exactly rounded sums added with math.fsum.  Every step is the
+    unchanged oracle."""
+    import oracle
+    G = oracle.half_spectrum(p.image)
+    n = p.image.shape[0]
+    b = np.linspace(0, p.u.size, nthreads + 1).astype(np.int64)
+
+    def part(k):
+        s = slice(int(b[k]), int(b[k + 1]))
+        vis = oracle.sample_spectrum(G, n, p.dxy, p.u[s], p.v[s], p.dRA, p.dDec, p.PA)
+        return oracle.chi2(vis, re[s], im[s], p.w[s])
+
+    return math.fsum(pool.map(part, range(nthreads)))
+
+
 def cpu_baseline(p, re, im, evals: int):
-    times = []
+    """The FP64 oracle timed on the host cores on full evaluations of the
+    workload: single-threaded (numpy as it stands) and on all usable cores
+    (oracle_eval_threads), at least three evaluations each, min and median."""
+    from concurrent.futures import ThreadPoolExecutor
+    host = host_info()
+    evals = max(3, evals)
+    single = []
     for _ in range(evals):
         t0 = time.perf_counter()
         oracle_eval(p, re, im)
-        times.append(time.perf_counter() - t0)
-    dt = sum(times)
-    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{evals} full FP64 oracle chi2_image evaluation(s) of the same workload "
-                      f"(numpy, single thread), {dt:.1f} s",
-            "seconds_per_eval": {"min": min(times), "median": statistics.median(times)}}
+        single.append(time.perf_counter() - t0)
+    nthr = max(1, host["usable_cpus"] or 1)
+    allc = []
+    with ThreadPoolExecutor(nthr) as pool:
+        oracle_eval_threads(p, re, im, pool, nthr)  # warm the pool
+        for _ in range(evals):
+            t0 = time.perf_counter()
+            oracle_eval_threads(p, re, im, pool, nthr)
+            allc.append(time.perf_counter() - t0)
+    med = statistics.median(allc)
+    return {"value": 1.0 / med, "unit": UNIT, "cores": nthr, "kind": "oracle",
+            "sample": f"{evals} full FP64 oracle chi2_image evaluations of the same workload on "
+                      f"{nthr} threads (image FFT in one numpy call, then sampling and chi2 on "
+                      f"{nthr} contiguous shares of the points); value = 1 / median",
+            "seconds_per_eval": {"min": min(allc), "median": med},
+            "single_thread": {"value": 1.0 / statistics.median(single), "cores": 1,
+                              "seconds_per_eval": {"min": min(single),
+                                                   "median": statistics.median(single)},
+                              "evals": evals},
+            "host": host}
 
 
-REF_SAMPLE_POINTS = 100_000  # uv points per reference step (about 15 ms of oracle work)
+REF_SAMPLE_POINTS = 100_000   # uv points per reference step when full evaluations do not fit
+REF_BUDGET_S = 150.0          # whole --steps K --warmup W run of the reference arm
 
 
 def run_reference(args):
-    """The FP64 oracle on the host cores, on the same workload.  One full
-    evaluation is an FFT of the image (fixed cost, timed once after warm-up)
-    plus sampling and chi-square of M points.  Each timed step evaluates a
-    sample of REF_SAMPLE_POINTS consecutive points through the oracle's own
-    sample_spectrum and chi2, so that --steps K ends within minutes for any
-    K; the reported rate is 1 / (FFT time + mean step time x M / sample)."""
+    """The FP64 oracle on the host cores, on the same workload and metric.
+
+    Each step is one full evaluation on all usable cores (oracle_eval_threads)
+    when K + W of them fit in about REF_BUDGET_S seconds (the first warm-up
+    evaluation sets the estimate); the rate is then measured, 1 / mean step
+    time.  Otherwise (a very large --steps) each step samples and reduces
+    REF_SAMPLE_POINTS consecutive points after one timed image FFT, and the
+    rate is an estimate, FFT time + mean step time x M / sample, labelled so
+    in the line."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
@@ -250,40 +410,145 @@ def run_reference(args):
     rng = np.random.default_rng(7)
     re = rng.standard_normal(p.u.size)
     im = rng.standard_normal(p.u.size)
+    host = host_info()
+    nthr = max(1, host["usable_cpus"] or 1)
+    pool = ThreadPoolExecutor(nthr)
     t0 = time.perf_counter()
-    G = oracle.half_spectrum(p.image)
-    t_fft = time.perf_counter() - t0
-    m = min(REF_SAMPLE_POINTS, p.u.size)
-    nsamp = p.u.size // m
+    oracle_eval_threads(p, re, im, pool, nthr)
+    t_full = time.perf_counter() - t0
+    full = (args.steps + args.warmup) * t_full <= REF_BUDGET_S
+    if full:
+        for _ in range(max(0, args.warmup - 1)):
+            oracle_eval_threads(p, re, im, pool, nthr)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle_eval_threads(p, re, im, pool, nthr)
+        dt = time.perf_counter() - t0
+        value = args.steps / dt
+        sample = (f"each step: one full FP64 oracle chi2_image evaluation of the workload on "
+                  f"{nthr} threads (image FFT, then sampling and chi2 on {nthr} shares); "
+                  f"measured, value = steps / time")
+        estimate = False
+    else:
+        t0 = time.perf_counter()
+        G = oracle.half_spectrum(p.image)
+        t_fft = time.perf_counter() - t0
+        m = min(REF_SAMPLE_POINTS, p.u.size)
+        nsamp = p.u.size // m
 
-    def step(i):
-        lo = (i % nsamp) * m
-        sl = slice(lo, lo + m)
-        vis = oracle.sample_spectrum(G, NXY, p.dxy, p.u[sl], p.v[sl], p.dRA, p.dDec, p.PA)
-        return oracle.chi2(vis, re[sl], im[sl], p.w[sl])
+        def step(i):
+            lo = (i % nsamp) * m
+            sl = slice(lo, lo + m)
+            vis = oracle.sample_spectrum(G, NXY, p.dxy, p.u[sl], p.v[sl], p.dRA, p.dDec, p.PA)
+            return oracle.chi2(vis, re[sl], im[sl], p.w[sl])
 
-    for i in range(args.warmup):
-        step(i)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        step(i)
-    dt = time.perf_counter() - t0
-    per_eval = t_fft + (dt / args.steps) * (p.u.size / m)
-    value = 1.0 / per_eval
-    sample = (f"each step: oracle sampling + chi2 of {m} of the {p.u.size} points; "
-              f"image FFT timed once ({t_fft:.2f} s); full evaluation = FFT + step x {p.u.size // m}")
+        for i in range(args.warmup):
+            step(i)
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            step(i)
+        dt = time.perf_counter() - t0
+        value = 1.0 / (t_fft + (dt / args.steps) * (p.u.size / m))
+        nthr = 1
+        sample = (f"ESTIMATE: each step samples and reduces {m} of the {p.u.size} points on one "
+                  f"thread; image FFT timed once ({t_fft:.2f} s); value = 1 / (FFT + step x "
+                  f"{p.u.size // m}) (full evaluations would not fit {REF_BUDGET_S:.0f} s)")
+        estimate = True
+    pool.shutdown()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle",
+                         "sample": sample, "estimate": estimate, "host": host},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# accuracy against the FP64 oracle
+# ---------------------------------------------------------------------------
+def oracle_model_threads(p, pool, nthreads: int):
+    """The oracle's visibilities of the workload at its own geometry, computed
+    by the unchanged oracle on nthreads contiguous shares of the points."""
+    import oracle
+    G = oracle.half_spectrum(p.image)
+    n = p.image.shape[0]
+    b = np.linspace(0, p.u.size, nthreads + 1).astype(np.int64)
+    parts = pool.map(lambda k: oracle.sample_spectrum(G, n, p.dxy, p.u[b[k]:b[k + 1]],
+                                                      p.v[b[k]:b[k + 1]], p.dRA, p.dDec, p.PA),
+                     range(nthreads))
+    return np.concatenate(list(parts))
+
+
+def measure_accuracy(torch, ctx, dev, p, re_h, im_h):
+    """Error of each result against the FP64 oracle on the very inputs the
+    path sees (the workload's float32-rounded image, uv and weights; observed
+    data re_h, im_h as float32 values), for the float32 and float64 paths:
+
+    vis_normwise     max_k |V_k - V_oracle,k| / max_k |V_oracle,k|, all M points
+    vis_rms          sqrt(mean_k |V_k - V_oracle,k|^2) / max_k |V_oracle,k|
+    chi2_rel         |chi2 - chi2_oracle| / chi2_oracle, observed = model + noise
+    chi2_model_rms   observed = the oracle model itself: chi2 = sum_k w_k |dV_k|^2,
+                     reported as sqrt(chi2 / sum_k w_k) / max|V| (the weighted rms
+                     model error, with no noise term to hide it)
+    phase_max_abs    a unit point source at the phase centre has the constant
+                     spectrum 1 (exact in both precisions), so its visibilities
+                     are exp(2 pi i (u dRA + v dDec)) and the difference is the
+                     error of the phase factor alone: max_k |V_k - exp(i theta_k)|
+    """
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    nthr = max(1, host_info()["usable_cpus"] or 1)
+    with ThreadPoolExecutor(nthr) as pool:
+        model = oracle_model_threads(p, pool, nthr)
+    vmax = float(np.max(np.abs(model)))
+    theta = 2.0 * np.pi * (p.u * p.dRA + p.v * p.dDec)
+    unit = np.exp(1j * theta)
+    N = p.image.shape[0]
+    delta = np.zeros((N, N))
+    delta[N // 2, N // 2] = 1.0
+    out = {"reference": "FP64 oracle on the same float32-rounded inputs",
+           "geometry": {"dRA": p.dRA, "dDec": p.dDec, "PA": p.PA}}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+        img, u, v, w = d(p.image), d(p.u), d(p.v), d(p.w)
+        vis = ctx.sample_image(img, p.dxy, u, v, p.dRA, p.dDec, p.PA).double().cpu().numpy()
+        V = vis[:, 0] + 1j * vis[:, 1]
+        dV = np.abs(V - model)
+        obs = ctx.register(u, v, d(re_h), d(im_h), w)
+        c = ctx.chi2_image(img, p.dxy, obs, p.dRA, p.dDec, p.PA).item()
+        c_ref = oracle.chi2(model, re_h, im_h, p.w)
+        obs0 = ctx.register(u, v, d(model.real), d(model.imag), w)
+        c0 = ctx.chi2_image(img, p.dxy, obs0, p.dRA, p.dDec, p.PA).item()
+        vd = ctx.sample_image(d(delta), p.dxy, u, v, p.dRA, p.dDec, p.PA).double().cpu().numpy()
+        out[name] = {"vis_normwise": float(np.max(dV) / vmax),
+                     "vis_rms": float(np.sqrt(np.mean(dV * dV)) / vmax),
+                     "chi2_rel": abs(c - c_ref) / c_ref,
+                     "chi2_model_rms": float(np.sqrt(max(c0, 0.0) / np.sum(p.w)) / vmax),
+                     "phase_max_abs": float(np.max(np.abs(vd[:, 0] + 1j * vd[:, 1] - unit)))}
+        obs.close()
+        obs0.close()
+    out["gates"] = {"f32": {"vis_normwise": 1e-5, "chi2_rel": 1e-6},
+                    "f64": {"vis_normwise": 1e-12, "chi2_rel": 1e-12}}
+    return out
+
+
+def oracle_chi2_of(r, arrays):
+    """The FP64 oracle's chi-square of one batched or served request, on the
+    request's own float32 arrays (u, v, re, im, w)."""
+    import oracle
+    u, v, re, im, w = (np.asarray(t.double().cpu().numpy() if hasattr(t, "cpu") else t,
+                                  dtype=np.float64) for t in arrays)
+    if r.image is not None:
+        return oracle.chi2_image(r.image.double().cpu().numpy(), r.dxy, u, v, re, im, w, r.dRA,
+                                 r.dDec, r.PA, pb_fwhm=r.pb_fwhm)
+    return oracle.chi2_profile(r.intensity.double().cpu().numpy(), r.Rmin, r.dR, r.nxy, r.dxy,
+                               u, v, re, im, w, r.dRA, r.dDec, r.PA, r.inc)
 
 
 # ---------------------------------------------------------------------------
@@ -418,7 +683,7 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200)
     return res
 
 
-def measure_batched(torch, ctx, dev, flush, reps=3):
+def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
     """Spectral cube (128 Keplerian channels, nxy in {512, 1024, 2048}, M_c in
     [1e5, 2e6]) and 64 ring-profile walkers (nxy 1024, M 1e6 shared): one
     gal_chi2_batch per set, its CUDA-graph replay, sequential FP32 single
@@ -427,9 +692,10 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
     d32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
     sets = {}
     cube = synth.spectral_cube(n_chan=128, seed=3)
-    r32, r64 = [], []
+    r32, r64, arr_cube = [], [], []
     for ch in cube:
         t32 = [d32(a) for a in (ch.u, ch.v, ch.noise_re, ch.noise_im, ch.w)]
+        arr_cube.append(t32)
         o32 = ctx.register(*t32, z_order=True)
         o64 = ctx.register(*[t.double() for t in t32], z_order=True)
         img = d32(ch.image)
@@ -438,7 +704,7 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
                            PA=ch.PA))
     sets["cube"] = (r32, r64, "128 Keplerian-disc channels, nxy U{512,1024,2048}, "
                               "M_c U[1e5,2e6] (ALMA-like layout x channel frequency), "
-                              "observations registered in Z-order")
+                              "observations registered in Z-order", arr_cube)
     # the same channels, each through its own primary beam: FWHM 1.13 lambda_c / 12 m
     # (channel frequency: line at 100 GHz, channels 0.5 km/s apart, as in the cube)
     b32, b64 = [], []
@@ -449,7 +715,8 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
             dst.append(Request(src.obs, image=src.image, dxy=src.dxy, dRA=src.dRA,
                                dDec=src.dDec, PA=src.PA, pb_fwhm=theta))
     sets["cube_beams"] = (b32, b64, "the same 128 channels, each with its primary beam "
-                                    "(FWHM 1.13 lambda_c / 12 m, applied in the row FFT)")
+                                    "(FWHM 1.13 lambda_c / 12 m, applied in the row FFT)",
+                          arr_cube)
     q = synth.profile_problem(nxy=1024, M=1_000_000, nr=8192, seed=1)
     t32 = [d32(a) for a in (q.u, q.v, q.noise_re, q.noise_im, q.w)]
     o32 = ctx.register(*t32, z_order=True)
@@ -462,9 +729,9 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
         w32.append(Request(o32, intensity=I, **kw))
         w64.append(Request(o64, intensity=I.double(), **kw))
     sets["walkers"] = (w32, w64, "64 ring-profile walkers, nxy 1024, nr 8192, one M=1e6 "
-                                 "observation shared, registered in Z-order")
+                                 "observation shared, registered in Z-order", [t32] * len(w32))
     res = {}
-    for name, (a32, a64, desc) in sets.items():
+    for name, (a32, a64, desc, arrays) in sets.items():
         n = len(a32)
         out = ctx.chi2_batch(a32)                      # first call tunes the launch shape
         seq = torch.stack([_single(ctx, r) for r in a32])
@@ -482,6 +749,10 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
         ms_64 = _timed(torch, lambda: [_single(ctx, r, out=outs[k]) for k, r in enumerate(a64)],
                        1, flush)
         rel = ((out - ref64).abs() / ref64.abs()).max().item()
+        # against the FP64 oracle: the first n_oracle requests of the set
+        got = out.cpu().numpy()
+        refs = [oracle_chi2_of(a32[k], arrays[k]) for k in range(n_oracle)]
+        rel_oracle = max(abs(got[k] - refs[k]) / abs(refs[k]) for k in range(n_oracle))
         res[name] = {
             "workload": desc, "requests": n,
             "batched_evals_per_s": 1000.0 * n / ms_b, "graph_evals_per_s": 1000.0 * n / ms_g,
@@ -490,6 +761,8 @@ def measure_batched(torch, ctx, dev, flush, reps=3):
             "ms_per_batch": ms_b, "launches_per_batch": launches,
             "bitwise_equal_to_single_calls": bool(torch.equal(out, seq)),
             "max_rel_err_vs_fp64_path": rel,
+            "max_chi2_rel_err_vs_oracle": rel_oracle,
+            "oracle_checked_requests": n_oracle,
         }
         g.close()
     return res
@@ -551,15 +824,28 @@ def measure_serving(torch, dev, seconds=2.0, rate=2000.0, seed=21):
             while time.perf_counter() - t0 < ta:
                 pass
             tickets.append(srv.submit(r))
-        return np.array([srv.wait(tk)[1] for tk in tickets])
+        got = [srv.wait(tk) for tk in tickets]
+        return np.array([g[1] for g in got]), np.array([g[0] for g in got])
 
     # warm-up: the first 20% of the trace (every worker grows its workspaces)
     n_warm = max(1, n // 5)
     serve(reqs32[:n_warm], arrivals[:n_warm])
-    lat = serve(reqs32, arrivals)
+    lat, chi2_served = serve(reqs32, arrivals)
     span = max(float(np.max(arrivals + lat)), float(arrivals[-1]))
     st = srv.stats()
     srv.close()
+    # served results against the FP64 oracle: the first request of each kind
+    # at the largest and smallest sizes in the trace
+    picks = []
+    for want in ((True, 4096), (False, 4096), (True, 256), (False, 256)):
+        k = next((i for i, (_, sp) in enumerate(trace) if (sp["image"], sp["nxy"]) == want), None)
+        if k is not None:
+            picks.append(k)
+    served_rel = 0.0
+    for i in picks:
+        r = reqs32[i]
+        ref = oracle_chi2_of(r, data32[trace[i][0]]._tensors)
+        served_rel = max(served_rel, abs(chi2_served[i] - ref) / abs(ref))
     # plain FP64: one single call at a time, in arrival order
     imgs64 = {s: im.double() for s, im in imgs.items()}
     prof64 = prof.double()
@@ -589,7 +875,9 @@ def measure_serving(torch, dev, seconds=2.0, rate=2000.0, seed=21):
         "fp32_server": {"p50_ms": ms(lat, 50), "p99_ms": ms(lat, 99), "mean_ms": float(lat.mean() * 1e3),
                         "throughput_req_per_s": n / span, "launches": st["launches"],
                         "max_inflight": st["max_inflight"], "peak_hbm_bytes": st["peak_bytes"],
-                        "slots": 4, "max_batch": 16, "budget_bytes": 150 * 10**9},
+                        "slots": 4, "max_batch": 16, "budget_bytes": 150 * 10**9,
+                        "max_chi2_rel_err_vs_oracle": served_rel,
+                        "oracle_checked_requests": len(picks)},
         "plain_fp64": {"p50_ms": ms(lat64, 50), "p99_ms": ms(lat64, 99),
                        "mean_ms": float(lat64.mean() * 1e3), "throughput_req_per_s": n / span64},
         "latency": "host clock, submit to result in host memory",
@@ -645,6 +933,7 @@ def run_gpu(args):
         flush.zero_()
         flush_rd.sum(dtype=torch.int32)
 
+    clk = ClockSampler(dev.index).start()
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize(dev)
@@ -668,20 +957,22 @@ def run_gpu(args):
     # dependent launch of the next kernel.  Its stage times are collected
     # between steps (outside the step events).
     dom_ms, dom_n = 0.0, 0
-    with ClockSampler(dev.index if world == 1 else local) as clk:
-        for i in range(args.steps):
-            flush_l2()
-            sample = i % 10 == min(5, args.steps - 1)
-            if sample:
-                ctx.set_stage_timing(True, stages=[dom])
-            ev[i][0].record(stream)
-            step(i)
-            ev[i][1].record(stream)
-            if sample:
-                t = ctx.stage_times()[dom]
-                dom_ms, dom_n = dom_ms + t[0], dom_n + t[1]
-                ctx.set_stage_timing(False)
-        torch.cuda.synchronize(dev)
+    clk.begin()
+    for i in range(args.steps):
+        flush_l2()
+        sample = i % 10 == min(5, args.steps - 1)
+        if sample:
+            ctx.set_stage_timing(True, stages=[dom])
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+        if sample:
+            t = ctx.stage_times()[dom]
+            dom_ms, dom_n = dom_ms + t[0], dom_n + t[1]
+            ctx.set_stage_timing(False)
+    torch.cuda.synchronize(dev)
+    clk.end()
+    clk.stop()
     stage = {s: (0.0, 0) for s in range(4)}
     stage[dom] = (dom_ms, dom_n)
     gpu_launches = ctx.launch_count() - launches0
@@ -744,9 +1035,12 @@ def run_gpu(args):
     traffic = measured_traffic(kernels[dom], full)
 
     base = None
+    re_h, im_h = re.double().cpu().numpy(), im.double().cpu().numpy()
     if world == 1 and args.cpu_evals > 0:
-        base = cpu_baseline(p, re.double().cpu().numpy(), im.double().cpu().numpy(),
-                            evals=args.cpu_evals)
+        base = cpu_baseline(p, re_h, im_h, evals=args.cpu_evals)
+    accuracy = None
+    if world == 1 and not args.no_accuracy:
+        accuracy = measure_accuracy(torch, ctx, dev, p, re_h, im_h)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -777,6 +1071,8 @@ def run_gpu(args):
     }
     if base is not None:
         line["cpu_baseline"] = base
+    if accuracy is not None:
+        line["accuracy"] = accuracy
     if world == 1 and not args.no_extras:
         extras = set(args.extras.split(","))
         if "plane" in extras:
@@ -793,25 +1089,156 @@ def run_gpu(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# one evaluation split over ranks (uv points sharded, one exchange per step)
+# ---------------------------------------------------------------------------
+def shard_loop(local_chi2, steps: int, world: int, device, group=None, before=None,
+               events=None):
+    """Run `steps` sharded evaluations.  local_chi2(i) enqueues this rank's
+    partial chi-square of step i and returns it as a 0-d float64 tensor on
+    `device`; the partials are all-gathered on the device, one double per rank
+    per step, into a [steps, world] buffer, and summed in rank order with
+    math.fsum once the loop is over.  before(i) runs ahead of each step (the
+    L2 flush); events[i] = (start, end) CUDA events bracket step i's partial
+    and exchange.  Returns every step's total."""
+    import torch
+    import torch.distributed as dist
+    gathered = torch.zeros((steps, world), dtype=torch.float64, device=device)
+    for i in range(steps):
+        if before is not None:
+            before(i)
+        if events is not None:
+            events[i][0].record()
+        part = local_chi2(i).reshape(1)
+        if world > 1:
+            dist.all_gather([gathered[i, r:r + 1] for r in range(world)], part, group=group)
+        else:
+            gathered[i, 0:1].copy_(part)
+        if events is not None:
+            events[i][1].record()
+    return [math.fsum(row) for row in gathered.cpu().tolist()]
+
+
+def run_shard(args):
+    """One chi2_image evaluation of the workload split over the ranks: every
+    rank transforms the same image and evaluates its contiguous share of the
+    5e6 uv points; one all-gather of one double per rank per step; the total is
+    the same on every rank.  Strong scaling: value = whole evaluations per
+    second of the job."""
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1709_06999_gb300 import Context, shard
+
+    p = make_problem(seed=2)   # the same evaluation on every rank
+    ctx = Context(dev.index)
+    d = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    img = d(p.image)
+    u, v, w = d(p.u), d(p.v), d(p.w)
+    model = ctx.sample_image(img, p.dxy, u, v, p.dRA, p.dDec, p.PA)
+    re = (model[:, 0] + d(p.noise_re)).contiguous()
+    im = (model[:, 1] + d(p.noise_im)).contiguous()
+    lo, hi = shard.shard_bounds(u.numel(), world, rank)
+    obs = ctx.register(u[lo:hi], v[lo:hi], re[lo:hi], im[lo:hi], w[lo:hi])
+    partial = torch.empty((), dtype=torch.float64, device=dev)
+    prng = np.random.default_rng(11)
+    params = [(float(a), float(b), float(c)) for a, b, c in
+              zip(prng.uniform(-0.1, 0.1, 8) * math.pi / 648000,
+                  prng.uniform(-0.1, 0.1, 8) * math.pi / 648000, prng.uniform(0, math.pi, 8))]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush_rd = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def local_chi2(i):
+        ctx.chi2_image(img, p.dxy, obs, *params[i % len(params)], out=partial)
+        return partial
+
+    def flush_l2(i):
+        flush.zero_()
+        flush_rd.sum(dtype=torch.int32)
+
+    shard_loop(local_chi2, args.warmup, world, dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clk = ClockSampler(dev.index).start()
+    launches0 = ctx.launch_count()
+    clk.begin()
+    totals = shard_loop(local_chi2, args.steps, world, dev, before=flush_l2, events=ev)
+    torch.cuda.synchronize(dev)
+    clk.end()
+    clk.stop()
+    gpu_launches = ctx.launch_count() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    # the same evaluation on one rank's GPU over all points: equal to rounding
+    full = None
+    if rank == 0:
+        obs_all = ctx.register(u, v, re, im, w)
+        full = ctx.chi2_image(img, p.dxy, obs_all, *params[0]).item()
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": 1000.0 / ms_per_step, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nxy": NXY, "M": M_UV,
+                       "l2": "flushed before every step (256 MiB write + 256 MiB read)",
+                       "parallelism": f"uv points sharded x{world}, one all-gather of one "
+                                      "double per rank per step", "mode": "shard"},
+            "chi2_step0": totals[0], "chi2_one_gpu_all_points": full,
+            "rel_diff_vs_one_gpu": abs(totals[0] - full) / abs(full),
+            "gpu_launches": gpu_launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-evals", type=int, default=10)
+    ap.add_argument("--cpu-evals", type=int, default=3)
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the per-result errors against the FP64 oracle")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the beam/full-plane, batched (cube, walkers) and serving "
                          "measurements")
     ap.add_argument("--extras", default="plane,next,batched,serving",
                     help="comma-separated extra measurements to run after the bench line "
                          "(plane, next, batched, serving)")
+    ap.add_argument("--mode", default="replicas", choices=["replicas", "shard"],
+                    help="replicas: independent evaluations per rank (weak scaling, the "
+                         "headline); shard: one evaluation's uv points split over the ranks "
+                         "(strong scaling)")
     ap.add_argument("--variant", default="plain", choices=sorted(VARIANTS),
                     help="options of the timed chi2_image step (plain: the headline line)")
+    ap.add_argument("--clock-sampler", nargs=2, metavar=("TARGET", "PERIOD"),
+                    help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.clock_sampler:
+        return nvml_sample_loop(args.clock_sampler[0], float(args.clock_sampler[1]))
     args.warmup = max(3, args.warmup)   # the timing rules need at least 3 warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "shard":
+        return run_shard(args)
     return run_gpu(args)
 
 

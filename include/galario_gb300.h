@@ -512,7 +512,15 @@ int gal_get_image_size_f64(gal_ctx* ctx, const double* u, const double* v, int64
  * device address; make that first call before any stream capture.  Every call
  * uses the same array and leaves its contents behind (each call re-initialises
  * what it needs), so calls that may overlap on the GPU -- other streams, other
- * host threads -- race with each other and must be serialised by the caller. */
+ * host threads -- race with each other and must be serialised by the caller.
+ * Errors: argument errors return GAL_E_INVAL and enqueue nothing.  A bounded
+ * device wait that gives up (never expected) cannot be reported through a
+ * context here, so the call then writes NaN to *chi2_out.
+ * The window of the spectrum is always read through L2 and clamped as at the
+ * grid's edge, with four 256-thread gather blocks per SM: the result is bitwise
+ * gal_chi2_image_f32's when that call takes the same shape (a window wider
+ * than its 200 KB shared-memory budget that reaches the first row), and equal
+ * to rounding otherwise. */
 int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dxy, double dRA, double dDec,
                                double PA, const float* u, const float* v, const float* re,
                                const float* im, const float* w, int64_t M, double* chi2_out,

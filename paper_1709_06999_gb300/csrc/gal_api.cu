@@ -712,8 +712,22 @@ int chi2_image_host_async_t(gal_ctx* ctx, const T* image_host, int nxy, double d
   return GAL_OK;
 }
 
-std::once_flag g_init_once;
-cudaError_t g_init_err = cudaSuccess;
+// Kernel attributes (dynamic shared-memory limits) are per device: set them
+// once on each device a context is created on, with that device current.
+constexpr int kInitDevices = 64;
+std::mutex g_init_mutex;
+bool g_init_done[kInitDevices] = {};
+
+int init_current_device(int device) {
+  if (device < 0 || device >= kInitDevices) return GAL_E_DEVICE;
+  std::lock_guard<std::mutex> lk(g_init_mutex);
+  if (g_init_done[device]) return GAL_OK;
+  cudaError_t e = gal::Launch<float>::init();
+  if (e == cudaSuccess) e = gal::Launch<double>::init();
+  if (e != cudaSuccess) return GAL_E_DEVICE;  // e.g. no sm_103a image for this GPU
+  g_init_done[device] = true;
+  return GAL_OK;
+}
 
 }  // namespace
 
@@ -1128,11 +1142,7 @@ int gal_create(gal_ctx** out, int device) {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return GAL_E_DEVICE;
   if (cudaSetDevice(device) != cudaSuccess) return GAL_E_DEVICE;
-  std::call_once(g_init_once, [] {
-    g_init_err = gal::Launch<float>::init();
-    if (g_init_err == cudaSuccess) g_init_err = gal::Launch<double>::init();
-  });
-  if (g_init_err != cudaSuccess) return GAL_E_DEVICE;  // e.g. no sm_103a image for this GPU
+  if (const int st = init_current_device(device); st != GAL_OK) return st;
   gal_ctx* ctx = new (std::nothrow) gal_ctx;
   if (!ctx) return GAL_E_NOMEM;
   ctx->device = device;

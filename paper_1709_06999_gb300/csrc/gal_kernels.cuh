@@ -865,12 +865,14 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
     yh = -yh;
     yl = -yl;
   }
-  // cell = floor(hi); fraction = (hi - cell) + lo, saturated to [0, 1]: when
-  // hi sits within |lo| of an integer the neighbouring cell would be exact,
-  // and the saturated fraction differs from it by at most |lo| (one ulp)
+  // cell = floor(hi); fraction = (hi - cell) + lo.  When hi sits within |lo|
+  // of an integer the fraction leaves [0, 1] by at most |lo| (one ulp of hi),
+  // a linear extrapolation across the node that equals the neighbouring
+  // cell's interpolation to that order.  Every cell path computes the
+  // fraction this way, so the sampling and chi-square kernels agree bit for bit.
   const float cf = floorf(xh), rf = floorf(yh);
-  float fu = __saturatef((xh - cf) + xl);
-  float fv = __saturatef((yh - rf) + yl);
+  float fu = (xh - cf) + xl;
+  float fv = (yh - rf) + yl;
   int c = FULL ? (int)fmaxf(fminf(cf, 32768.f), -32768.f) + w.cofs : (int)fminf(cf, 32768.f);
   int r = (int)fmaxf(fminf(rf, 32768.f), -32768.f) + w.rofs;
   if constexpr (EDGE) {
@@ -994,8 +996,10 @@ __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const W
   float cf, rf;
   int c = floor_fma(xh, cf) + (FULL ? w.cofs : 0);
   int r = floor_fma(yh, rf) + w.rofs;
-  float fu = __saturatef((xh - cf) + xl);
-  float fv = __saturatef((yh - rf) + yl);
+  // fraction as in sample_point: (hi - cell) + lo, not clamped, so that this
+  // path and cell_pair_pruned give the same value for every in-window point
+  float fu = (xh - cf) + xl;
+  float fv = (yh - rf) + yl;
   if constexpr (EDGE) {
     if (FULL && c < 0) {
       c = 0;
@@ -1799,8 +1803,10 @@ cudaError_t Launch<T>::gather(const void* Gw, const GatherParams& gp, const doub
         le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes, ma);
     } else {
       constexpr auto kern = gather_kernel<T, CH, SM, ED, 1, false>;
-      le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes,
-                            MultiArg<T, false>{});
+      le = ensure_smem_attr<kern>(smem);
+      if (le == cudaSuccess)
+        le = launch_dependent(kern, dim3(grid), dim3(threads), smem, st, jb, nodes,
+                              MultiArg<T, false>{});
     }
   };
   using TT = std::true_type;

@@ -72,6 +72,13 @@ int setup_current_device(DeviceSetup** out) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// After the gather: a bounded wait of the row pass that gave up (the error
+// word is non-zero) left the spectrum incomplete, so the result is replaced by
+// NaN.  With no context there is no gal_check to report it; the NaN does.
+__global__ void noalloc_status_kernel(const int* __restrict__ err, double* __restrict__ chi2_out) {
+  if (*err != 0) *chi2_out = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 }  // namespace
 
 extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dxy, double dRA,
@@ -125,5 +132,6 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
   if (gal::Launch<float>::gather(Gw, gp, rho2, u, v, re, im, w, M, nullptr, partials, counter,
                                  chi2_out, 0, true, s->gather_blocks, nullptr, cs) != cudaSuccess)
     return GAL_E_CUDA;
-  return GAL_OK;
+  noalloc_status_kernel<<<1, 1, 0, cs>>>(err, chi2_out);
+  return cudaGetLastError() == cudaSuccess ? GAL_OK : GAL_E_CUDA;
 }

@@ -297,8 +297,11 @@ static int add_data(gal_server* s, const void* u, const void* v, const void* re,
   if (!s || !out || M < 0) return GAL_E_INVAL;
   const size_t bytes = 5 * (size_t)M * (size_t)rb;
   {
+    // reserve the bytes before registering, so that concurrent add_data
+    // calls cannot pass the check together and overrun the budget
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->data_bytes + bytes > s->budget) return GAL_E_NOMEM;
+    s->data_bytes += bytes;
   }
   cudaSetDevice(s->device);
   // z_order: the library keeps its own copies (the budget charges the same
@@ -312,10 +315,12 @@ static int add_data(gal_server* s, const void* u, const void* v, const void* re,
               : f64(s->primary, static_cast<const double*>(u), static_cast<const double*>(v),
                     static_cast<const double*>(re), static_cast<const double*>(im),
                     static_cast<const double*>(w), M, nullptr, out);
-  if (st != GAL_OK) return st;
   std::lock_guard<std::mutex> lk(s->mu);
+  if (st != GAL_OK) {
+    s->data_bytes -= bytes;  // give the reservation back
+    return st;
+  }
   s->data.push_back(*out);
-  s->data_bytes += bytes;
   return GAL_OK;
 }
 

@@ -58,11 +58,44 @@ def test_algorithmic_bytes():
 def test_cpu_baseline_fields(monkeypatch):
     import time
     monkeypatch.setattr(bench, "oracle_eval", lambda p, re, im: time.sleep(0.01))
+    monkeypatch.setattr(bench, "oracle_eval_threads",
+                        lambda p, re, im, pool, n: time.sleep(0.005))
     b = bench.cpu_baseline(None, None, None, 3)
-    assert b["kind"] == "oracle" and b["cores"] == 1 and b["unit"] == "evals/s"
+    assert b["kind"] == "oracle" and b["unit"] == "evals/s"
+    assert b["cores"] == b["host"]["usable_cpus"] >= 1
     s = b["seconds_per_eval"]
-    assert 0.009 < s["min"] <= s["median"] < 1.0
-    assert 1.0 < b["value"] <= 1.0 / s["min"]
+    assert 0.004 < s["min"] <= s["median"] < 1.0
+    assert abs(b["value"] - 1.0 / s["median"]) < 1e-9
+    one = b["single_thread"]
+    assert one["cores"] == 1 and one["evals"] == 3
+    assert 0.009 < one["seconds_per_eval"]["min"] <= one["seconds_per_eval"]["median"] < 1.0
+    assert set(b["host"]) == {"cpu_model", "nproc", "usable_cpus"}
+
+
+def test_host_info():
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and 1 <= h["usable_cpus"] <= h["nproc"]
+    assert h["cpu_model"] is None or isinstance(h["cpu_model"], str)
+
+
+def test_clock_samples_summary():
+    t0 = 1000.0
+    lines = [f"{t0 - 0.01} 1980 2070 300.0 1",       # before the region, idle
+             f"{t0 + 0.0002} 2070 2070 700.5 0",
+             f"{t0 + 0.0007} 2055 2070 900.0 4",      # sw_power_cap
+             "garbage line",
+             f"{t0 + 0.05} 2070 2070 200.0 1"]        # after the region
+    s = bench.parse_clock_samples(lines, t0, t0 + 0.001)
+    assert s["samples"] == 2 and s["window"] == "timed region"
+    assert s["sm_mhz"] == 2062.5 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["power_w_max"] == 900.0
+    # a region shorter than the sampling period: the neighbouring samples stand in
+    s = bench.parse_clock_samples(lines, t0 + 0.001, t0 + 0.0011)
+    assert s["samples"] == 2 and s["window"].startswith("nearest")
+    # hardware slowdown bits are reported by name
+    s = bench.parse_clock_samples([f"{t0} 1500 2070 1400.0 {0x8 | 0x40}"], t0, t0)
+    assert s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.parse_clock_samples([], 0, 1)["reasons"] == ["unavailable"]
 
 
 def test_fft_equivalent():

@@ -81,6 +81,55 @@ def test_two_gloo_ranks_match_the_whole_sum():
     assert abs(got[0] - whole) <= 1e-12 * abs(whole)
 
 
+def _bench_rank(rank, world, port, q):
+    """bench.shard_loop, the timed loop of `bench.py --mode shard`, on a gloo
+    rank: each step evaluates this rank's share with the oracle (another
+    model amplitude per step) and the partials go through the loop's exchange."""
+    import sys
+    import torch
+    import torch.distributed as dist
+    import oracle
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    p = synth.small_image_problem(nxy=64, M=4_003, seed=8)
+    lo, hi = shard.shard_bounds(p.u.size, world, rank)
+    flushed = []
+
+    def local(i):
+        c = oracle.chi2_image(p.image * (1.0 + 0.1 * i), p.dxy, p.u[lo:hi], p.v[lo:hi],
+                              p.noise_re[lo:hi], p.noise_im[lo:hi], p.w[lo:hi], p.dRA, p.dDec,
+                              p.PA)
+        return torch.tensor(c, dtype=torch.float64)
+
+    totals = bench.shard_loop(local, 3, world, torch.device("cpu"), before=flushed.append)
+    q.put((rank, totals, flushed))
+    dist.destroy_process_group()
+
+
+def test_bench_shard_loop_two_gloo_ranks():
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_rank, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    got = {r: (t, f) for r, t, f in (q.get(timeout=120) for _ in procs)}
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    p = synth.small_image_problem(nxy=64, M=4_003, seed=8)
+    assert got[0][0] == got[1][0]                        # the same totals on both ranks
+    assert got[0][1] == got[1][1] == [0, 1, 2]           # the flush hook ran before each step
+    for i, total in enumerate(got[0][0]):
+        whole = oracle.chi2_image(p.image * (1.0 + 0.1 * i), p.dxy, p.u, p.v, p.noise_re,
+                                  p.noise_im, p.w, p.dRA, p.dDec, p.PA)
+        assert abs(total - whole) <= 1e-12 * abs(whole)
+
+
 @pytest.mark.gpu
 def test_sharded_observation_on_one_gpu_rank():
     """World size 1 on the GPU: the sharded call equals the plain call."""
