@@ -952,30 +952,30 @@ def run_gpu(args):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
-    # Inside the timed region the dominant kernel is bracketed by events on
-    # every tenth step only: events between kernels would also stop the
-    # dependent launch of the next kernel.  Its stage times are collected
-    # between steps (outside the step events).
-    dom_ms, dom_n = 0.0, 0
+    # The timed region holds exactly K plain steps.  The dominant kernel's own
+    # launch time is measured afterwards on separate steps of the same kind
+    # (L2 flushed, events around that kernel alone): events between kernels
+    # would also stop the dependent launch of the next kernel.
     clk.begin()
     for i in range(args.steps):
         flush_l2()
-        sample = i % 10 == min(5, args.steps - 1)
-        if sample:
-            ctx.set_stage_timing(True, stages=[dom])
         ev[i][0].record(stream)
         step(i)
         ev[i][1].record(stream)
-        if sample:
-            t = ctx.stage_times()[dom]
-            dom_ms, dom_n = dom_ms + t[0], dom_n + t[1]
-            ctx.set_stage_timing(False)
     torch.cuda.synchronize(dev)
     clk.end()
     clk.stop()
+    gpu_launches = ctx.launch_count() - launches0
+    dom_ms, dom_n = 0.0, 0
+    ctx.set_stage_timing(True, stages=[dom])
+    for i in range(max(10, min(args.steps, 50))):
+        flush_l2()
+        step(i)
+    t = ctx.stage_times()[dom]
+    dom_ms, dom_n = t[0], t[1]
+    ctx.set_stage_timing(False)
     stage = {s: (0.0, 0) for s in range(4)}
     stage[dom] = (dom_ms, dom_n)
-    gpu_launches = ctx.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if world > 1:
@@ -1061,9 +1061,10 @@ def run_gpu(args):
                      "avg_launch_us": 1000 * avg[dom]},
         "stages_us": {STAGES[s]: round(1000 * cal[s][0] / cal[s][1], 2)
                       for s in range(4) if cal[s][1]},
-        "stages_note": "per-stage event times from 3 untimed calibration steps; in the "
-                       "timed region events bracket only the dominant stage, on every "
-                       "tenth step",
+        "stages_note": "per-stage event times from 3 untimed calibration steps (each with "
+                       "about 4 us of event overhead); the dominant kernel's average launch "
+                       "time (roofline) comes from 10-50 further steps after the timed "
+                       "region, events around that kernel alone",
         "fp64_plain": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
                        "note": "same workload through the float64 entry point, single calls"},
         "flops": fft_equivalent(NXY, value),

@@ -359,9 +359,9 @@ template <typename C> __device__ __forceinline__ C r2c_unpack(C zk, C zmk, C w) 
 // Launch shape of the length-L passes: G sequences per block (at least 128
 // threads), each with a shared-memory region of RS complex (padded, rounded
 // to 16 bytes so that bulk copies into it stay aligned).
-template <typename T, int L, int NSEQ, int MINT = 128> struct Shape3 {
+template <typename T, int L, int NSEQ, int MINT = 128, int VV = FftV<T>::V> struct Shape3 {
   using C = cplx_t<T>;
-  static constexpr int V = FftV<T>::V;
+  static constexpr int V = VV;
   using P = P3<L, V>;
   static constexpr int G0 = P::T >= MINT ? 1 : MINT / P::T;
   static constexpr int G = G0 < NSEQ ? G0 : NSEQ;
@@ -388,9 +388,14 @@ template <int THREADS> constexpr int min_blocks_128regs() {
 // BEAM: multiply the pixels by the primary-beam tables; the kernel is then
 // launched as a programmatic dependent of beam_table_kernel and waits for it
 // only before the first table read (its image copies are already in flight).
-template <typename T, int LG, bool TMA, bool SWEEP, int K, bool BEAM = false>
-__global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG)>::threads,
-                                  min_blocks_128regs<Shape3<T, (1 << LG), (2 << LG)>::threads>())
+// MINT: least threads per block (rows per group G = MINT / threads per row,
+// at least one): the row-group shape.  NSLOT: row groups in the bulk-copy
+// ring (NSLOT - 1 stay in flight while one is transformed).  VR: values per
+// thread, the radix of every stage but the last.
+template <typename T, int LG, bool TMA, bool SWEEP, int K, bool BEAM = false, int MINT = 128,
+          int NSLOT = 2, int VR = FftV<T>::V>
+__global__ void __launch_bounds__(Shape3<T, (1 << LG), (2 << LG), MINT, VR>::threads,
+                                  min_blocks_128regs<Shape3<T, (1 << LG), (2 << LG), MINT, VR>::threads>())
 row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw,
                 int* __restrict__ err) {
   using C = cplx_t<T>;
@@ -404,7 +409,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
   const double S = jb.S;
   const T* __restrict__ beam = BEAM ? jb.beam : nullptr;
   constexpr int M = 1 << LG, N = 2 * M;
-  using SH = Shape3<T, M, N>;
+  using SH = Shape3<T, M, N, MINT, VR>;
   using P = typename SH::P;
   constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -461,20 +466,20 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
     }
   };
   if constexpr (TMA) {
+    static_assert(NSLOT >= 2 && NSLOT <= 8, "ring of 2 to 8 slots");
     C* slot0 = base;
-    C* work = base + 2 * G * RS;
+    C* work = base + NSLOT * G * RS;
     const int ngroups = N / G;
     const uint32_t half_bytes = (uint32_t)(M * sizeof(T));
     if (threadIdx.x == 0) {
-      mbar_init(&bars[0], 1);
-      mbar_init(&bars[1], 1);
+      for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
       mbar_init_fence();
     }
     __syncthreads();
     auto issue = [&](int it) {  // thread 0 only
       const int grp = blockIdx.x + it * gridDim.x;
       if (grp >= ngroups) return;
-      const int sl = it & 1;
+      const int sl = it % NSLOT;
       mbar_arrive_expect_tx(&bars[sl], 2u * half_bytes * (uint32_t)G);
       for (int rl = 0; rl < G; ++rl) {
         const T* src = image + (size_t)(((grp * G + rl) + M) & (N - 1)) * N;
@@ -483,21 +488,20 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
         bulk_load(dst + M, src, half_bytes, &bars[sl]);
       }
     };
-    if (threadIdx.x == 0) {
-      issue(0);
-      issue(1);
-    }
+    if (threadIdx.x == 0)
+      for (int k = 0; k < NSLOT; ++k) issue(k);
     if constexpr (BEAM) grid_dep_wait();  // the beam tables
     for (int it = 0;; ++it) {
       const int grp = blockIdx.x + it * gridDim.x;
       if (grp >= ngroups) break;
-      const int sl = it & 1;
-      const bool ok = mbar_wait(&bars[sl], (uint32_t)((it >> 1) & 1));
+      const int sl = it % NSLOT;
+      const bool ok = mbar_wait(&bars[sl], (uint32_t)((it / NSLOT) & 1));
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
           atomicOr(err, 2);
-          for (int k = it; k < it + 2; ++k)
-            if (blockIdx.x + k * gridDim.x < ngroups) mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1));
+          for (int k = it; k < it + NSLOT; ++k)
+            if (blockIdx.x + k * gridDim.x < ngroups)
+              mbar_wait(&bars[k % NSLOT], (uint32_t)((k / NSLOT) & 1));
         }
         return;
       }
@@ -513,7 +517,7 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
       // after the barrier that ends stage 0
       transform(v, work + (size_t)g * RS, slot, grp * G + g);
       __syncthreads();  // every read of this slot is done
-      if (threadIdx.x == 0) issue(it + 2);
+      if (threadIdx.x == 0) issue(it + NSLOT);
     }
   } else {
     C* A = base + (size_t)g * RS;
@@ -545,10 +549,11 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
 // an unpruned window is then written a row at a time with the block's G
 // adjacent columns side by side (whole 32-byte sectors, not one 8-byte value
 // per sector).
-template <typename T, int L> using ColShape3 = Shape3<T, L, (1 << 30), 256>;
+template <typename T, int L, int VC = FftV<T>::V> using ColShape3 = Shape3<T, L, (1 << 30), 256, VC>;
 
-template <typename T, int LG, int K>
-__global__ void __launch_bounds__(ColShape3<T, (1 << LG)>::threads)
+// VC: values per thread, the radix of every stage but the last
+template <typename T, int LG, int K, int VC = FftV<T>::V>
+__global__ void __launch_bounds__(ColShape3<T, (1 << LG), VC>::threads)
 col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>* __restrict__ tw) {
   const ColJob<T>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
   const cplx_t<T>* __restrict__ F1 = jb.F1;
@@ -558,7 +563,7 @@ col_fft3_kernel(const __grid_constant__ Jobs<ColJob<T>, K> jobs, const cplx_t<T>
   grid_dep_launch();  // the gather may start its prologue on the SMs we leave idle
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = ColShape3<T, N>;
+  using SH = ColShape3<T, N, VC>;
   using P = typename SH::P;
   constexpr int V = SH::V, TT = P::T, G = SH::G, RS = SH::RS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
