@@ -688,7 +688,7 @@ def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
     [1e5, 2e6]) and 64 ring-profile walkers (nxy 1024, M 1e6 shared): one
     gal_chi2_batch per set, its CUDA-graph replay, sequential FP32 single
     calls and sequential FP64 single calls of the same requests."""
-    from paper_1709_06999_gb300 import Request, synth
+    from paper_1709_06999_gb300 import Request, get_fft_radix, synth
     d32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)  # noqa: E731
     sets = {}
     cube = synth.spectral_cube(n_chan=128, seed=3)
@@ -763,6 +763,8 @@ def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
             "max_rel_err_vs_fp64_path": rel,
             "max_chi2_rel_err_vs_oracle": rel_oracle,
             "oracle_checked_requests": n_oracle,
+            "fft_plans": {str(nx): list(get_fft_radix(dev.index or 0, torch.float32, nx))
+                          for nx in sorted({int(r.nxy) for r in a32})},
         }
         g.close()
     return res

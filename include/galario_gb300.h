@@ -382,7 +382,31 @@ typedef struct gal_request {
  * different streams must not overlap.
  * Errors: GAL_E_INVAL if any request is invalid (nothing is launched then). */
 int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, void* stream);
+/* enable = 0 turns off the context's tuning: launch shapes of batches and the
+ * FFT plans of sides it is first to use (which then take the default). */
 int gal_set_batch_tuning(gal_ctx* ctx, int enable);
+
+/* FFT plans (an implementation choice; the paper's transform is any FFT,
+ * Sect. 4).  The row and column passes of a float32 image of side 32 .. 512
+ * exist at two radices (values per thread in the register-blocked stages):
+ * 16 and 8.  Which one runs is the plan of that side, one per device and
+ * precision for the whole process, so that single calls, batches, graphs,
+ * served requests and gal_chi2_image_noalloc_f32 compute a request with the
+ * same arithmetic (their results stay bitwise equal).  A side's plan is fixed
+ * at its first use by a context: the context times both radices of both
+ * passes on its workspace and stream (synchronising the stream once) and keeps
+ * radix 8 for a pass only if it is at least 5 % faster -- unless its tuning is
+ * off or the stream is being captured, when the side takes the default (16).
+ * Sides above 512 run at radix 16, float64 transforms at radix 8.  The two
+ * radices round differently, so results may differ in the last bits between
+ * processes whose plans differ; set the plan explicitly to fix them.
+ *   gal_set_fft_radix   sets the plan of (device, real_bytes 4 or 8, nxy):
+ *                       row_radix, col_radix 16 or 8 for float32 sides 32..512,
+ *                       16 for other float32 sides, 8 for float64.  It applies
+ *                       to calls enqueued afterwards.  GAL_E_INVAL otherwise.
+ *   gal_get_fft_radix   the plan of that side, or 0, 0 when it is not fixed yet. */
+int gal_set_fft_radix(int device, int real_bytes, int nxy, int row_radix, int col_radix);
+int gal_get_fft_radix(int device, int real_bytes, int nxy, int* row_radix, int* col_radix);
 
 /* A batch captured into a CUDA graph.  gal_chi2_batch_capture runs the batch
  * once on `stream` (workspace, twiddles and launch-shape tuning happen there)
@@ -516,11 +540,13 @@ int gal_get_image_size_f64(gal_ctx* ctx, const double* u, const double* v, int64
  * Errors: argument errors return GAL_E_INVAL and enqueue nothing.  A bounded
  * device wait that gives up (never expected) cannot be reported through a
  * context here, so the call then writes NaN to *chi2_out.
- * The window of the spectrum is always read through L2 and clamped as at the
- * grid's edge, with four 256-thread gather blocks per SM: the result is bitwise
- * gal_chi2_image_f32's when that call takes the same shape (a window wider
- * than its 200 KB shared-memory budget that reaches the first row), and equal
- * to rounding otherwise. */
+ * The transforms use the FFT plan of the side if one is fixed on the device
+ * (gal_set_fft_radix), the default radix otherwise.  The window of the
+ * spectrum is always read through L2 and clamped as at the grid's edge, with
+ * four 256-thread gather blocks per SM: the result is bitwise
+ * gal_chi2_image_f32's when that call takes the same shape (a window larger
+ * than its 200 KB shared-memory budget that spans every row) under the same
+ * plan, and equal to rounding otherwise. */
 int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dxy, double dRA, double dDec,
                                double PA, const float* u, const float* v, const float* re,
                                const float* im, const float* w, int64_t M, double* chi2_out,

@@ -8,5 +8,5 @@ CUDA kernels behind a C ABI (include/galario_gb300.h).
     chi2 = ctx.chi2_image(image, dxy, obs, dRA, dDec, PA)
 """
 from .api import (BatchGraph, Context, GalError, Observation, Request, Server,  # noqa: F401
-                  chi2_image, chi2_profile, default_context, get_image_size, sample_image,
-                  sample_profile, sweep)
+                  chi2_image, chi2_profile, default_context, get_fft_radix, get_image_size,
+                  sample_image, sample_profile, set_fft_radix, sweep)

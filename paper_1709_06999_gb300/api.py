@@ -588,6 +588,33 @@ class Server:
             pass
 
 
+def _real_bytes(dtype) -> int:
+    if dtype in (torch.float32, "float32", "f32", 4):
+        return 4
+    if dtype in (torch.float64, "float64", "f64", 8):
+        return 8
+    raise ValueError(f"dtype must be float32 or float64, got {dtype!r}")
+
+
+def set_fft_radix(device: int, dtype, nxy: int, row_radix: int, col_radix: int) -> None:
+    """Fix the FFT plan of image side nxy (radix of the row and the column
+    pass: 16 or 8 for float32 sides 32..512; 16 above; 8 for float64) on a
+    device for this process; see gal_set_fft_radix."""
+    lib = _native.load()
+    _check(None, lib.gal_set_fft_radix(int(device), _real_bytes(dtype), int(nxy), int(row_radix),
+                                       int(col_radix)))
+
+
+def get_fft_radix(device: int, dtype, nxy: int):
+    """(row radix, column radix) of side nxy on a device, or (0, 0) while no
+    call has fixed it."""
+    lib = _native.load()
+    r, c = ct.c_int(), ct.c_int()
+    _check(None, lib.gal_get_fft_radix(int(device), _real_bytes(dtype), int(nxy), ct.byref(r),
+                                       ct.byref(c)))
+    return r.value, c.value
+
+
 _default: dict[int, Context] = {}
 
 

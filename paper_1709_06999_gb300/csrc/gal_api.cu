@@ -287,6 +287,106 @@ template <typename T> int reserve_call(gal_ctx* ctx, int nxy, const CallOpts& o)
   return GAL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// FFT plans.  For float images of side 32 .. kAltRadixMaxSide the row and
+// column passes exist at radix 16 and at radix 8; the plan of a side says
+// which one runs.  There is one plan per device, side and precision for the
+// whole process, so single calls, batches, served requests and the
+// allocation-free entry point compute a request with the same arithmetic
+// (bitwise equal results).  A side's plan is fixed at its first use on a
+// context: timed on that context's workspace and stream when its tuning is on
+// and the stream is not being captured (each radix, each pass, best of three,
+// the smaller radix kept only when at least 5 % faster), otherwise the
+// default; gal_set_fft_radix overrides it.
+// ---------------------------------------------------------------------------
+namespace plans {
+constexpr int kDevices = 64;
+std::mutex mu;
+int table[kDevices][2][kMaxLog2 + 1][2] = {};  // [device][f64?][log2 side]{row, col}; 0: unset
+}  // namespace plans
+
+template <typename T> bool plan_tunable(int nxy) {
+  return sizeof(T) == 4 && nxy >= 32 && nxy <= gal::kAltRadixMaxSide;
+}
+
+// the plan of side nxy on `device` if chosen (returns false and the defaults otherwise)
+template <typename T> bool plan_lookup(int device, int nxy, int* rv, int* cv) {
+  *rv = *cv = gal::fft_radix_default<T>();
+  if (device < 0 || device >= plans::kDevices || !plan_tunable<T>(nxy)) return true;
+  std::lock_guard<std::mutex> lk(plans::mu);
+  const int* e = plans::table[device][prec_index<T>()][log2i(nxy)];
+  if (!e[0]) return false;
+  *rv = e[0];
+  *cv = e[1];
+  return true;
+}
+
+template <typename T> void plan_store(int device, int nxy, int rv, int cv, bool overwrite) {
+  if (device < 0 || device >= plans::kDevices || !plan_tunable<T>(nxy)) return;
+  std::lock_guard<std::mutex> lk(plans::mu);
+  int* e = plans::table[device][prec_index<T>()][log2i(nxy)];
+  if (e[0] && !overwrite) return;  // the first choice stands
+  e[0] = rv;
+  e[1] = cv;
+}
+
+// Time both radices of the row and column passes of side nxy on the
+// context's own workspace (its contents serve as input: only the time
+// matters) with the uv extent of the whole half spectrum.
+template <typename T> int tune_fft(gal_ctx* ctx, int nxy, cudaStream_t st, int* rv, int* cv) {
+  GAL_TRY(ensure<T>(ctx, nxy));
+  const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
+  const double big = 1e300;  // beyond any grid: nothing is pruned
+  GAL_CUDA(ctx, cudaMemcpyAsync(ctx->rho2, &big, sizeof(double), cudaMemcpyHostToDevice, st));
+  const T* img = static_cast<const T*>(ctx->Gw);
+  const double S = 1.0;
+  cudaEvent_t a = pool_event(ctx), b = pool_event(ctx);
+  auto best_of = [&](auto&& launch, float* ms) -> int {
+    *ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      GAL_CUDA(ctx, cudaEventRecord(a, st));
+      GAL_CUDA(ctx, launch());
+      ctx->launches++;
+      GAL_CUDA(ctx, cudaEventRecord(b, st));
+      GAL_CUDA(ctx, cudaEventSynchronize(b));
+      float t = 0.f;
+      GAL_CUDA(ctx, cudaEventElapsedTime(&t, a, b));
+      if (rep > 0 && t < *ms) *ms = t;  // the first run warms up
+    }
+    return GAL_OK;
+  };
+  const int r0 = gal::fft_radix_default<T>(), r1 = gal::kAltRadix;
+  float row[2], col[2];
+  for (int k = 0; k < 2; ++k) {
+    const int r = k ? r1 : r0;
+    GAL_TRY(best_of([&] {
+      return gal::Launch<T>::row_pass(img, nullptr, gal::SweepParams{}, nxy, tw, ctx->F1, ctx->rho2,
+                                      S, ctx->err, nullptr, st, r);
+    }, &row[k]));
+    GAL_TRY(best_of([&] {
+      return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, ctx->rho2, S, 0, false, st, r);
+    }, &col[k]));
+  }
+  ctx->event_pool.push_back(a);
+  ctx->event_pool.push_back(b);
+  *rv = row[1] < 0.95f * row[0] ? r1 : r0;
+  *cv = col[1] < 0.95f * col[0] ? r1 : r0;
+  return GAL_OK;
+}
+
+// Fix (or look up) the plan of side nxy before a call enqueues anything.
+template <typename T> int fft_plan(gal_ctx* ctx, int nxy, cudaStream_t st) {
+  int rv, cv;
+  if (plan_lookup<T>(ctx->device, nxy, &rv, &cv)) return GAL_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GAL_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
+  rv = cv = gal::fft_radix_default<T>();
+  if (ctx->batch_tuning && cap == cudaStreamCaptureStatusNone)
+    GAL_TRY(tune_fft<T>(ctx, nxy, st, &rv, &cv));
+  plan_store<T>(ctx->device, nxy, rv, cv, false);
+  return GAL_OK;
+}
+
 // FFT of the image (or of the swept profile) into the pruned window ctx->Gw;
 // `beam` multiplies the pixels (null: none), `full` keeps both signs of u.
 template <typename T>
@@ -296,12 +396,14 @@ int spectrum(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& s
   GAL_TRY(ensure<T>(ctx, nxy, full));
   const void* tw = ctx->tw[prec_index<T>()][log2i(nxy)];
   const double S = (double)nxy * dxy;
+  int rv, cv;
+  plan_lookup<T>(ctx->device, nxy, &rv, &cv);
   GAL_TRY(stage(ctx, 1, st, [&] {
     if (full) return gal::Plane<T>::rows(image, I, sp, nxy, tw, ctx->F1, rho2, S, beam, ctx->err, st);
-    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, beam, st);
+    return gal::Launch<T>::row_pass(image, I, sp, nxy, tw, ctx->F1, rho2, S, ctx->err, beam, st, rv);
   }));
   GAL_TRY(stage(ctx, 2, st, [&] {
-    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, full, st);
+    return gal::Launch<T>::col_pass(ctx->F1, ctx->Gw, nxy, tw, rho2, S, kc_hint, full, st, cv);
   }));
   return GAL_OK;
 }
@@ -320,6 +422,7 @@ int sample_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams
   if (!aligned(u, sizeof(T)) || !aligned(v, sizeof(T)) || !aligned(vis, 2 * sizeof(T)))
     return GAL_E_INVAL;
   GAL_TRY(reserve_call<T>(ctx, nxy, o));
+  GAL_TRY(fft_plan<T>(ctx, nxy, st));
   GAL_TRY(stage(ctx, 0, st, [&] {
     return gal::Launch<T>::extent(u, v, M, ctx->rho2, ctx->aux_blocks, st);
   }));
@@ -380,6 +483,7 @@ int chi2_impl(gal_ctx* ctx, const T* image, const T* I, const gal::SweepParams& 
   }
   using C = gal::cplx_t<T>;
   GAL_TRY(reserve_call<T>(ctx, nxy, o));
+  GAL_TRY(fft_plan<T>(ctx, nxy, st));
   const gal::Bounds bd = gal::make_bounds(d->rho2_host, (double)nxy * dxy, nxy);
   const T* beam;
   GAL_TRY(beam_tables<T>(ctx, o, nxy, dxy, dRA, dDec, PA, st, &beam));
@@ -1030,7 +1134,11 @@ int run_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_out, cu
   if (allow_setup) {
     for (const auto& b : pl.items[0]) GAL_TRY(ensure_twiddles<float>(ctx, b.N));
     for (const auto& b : pl.items[1]) GAL_TRY(ensure_twiddles<double>(ctx, b.N));
+    for (const auto& b : pl.items[0]) GAL_TRY(fft_plan<float>(ctx, b.N, st));
   }
+  // every request runs with the FFT plan of its side (the same as a single call's)
+  for (auto& b : pl.items[0]) plan_lookup<float>(ctx->device, b.N, &b.radix_row, &b.radix_col);
+  for (auto& b : pl.items[1]) plan_lookup<double>(ctx->device, b.N, &b.radix_row, &b.radix_col);
   gal::BatchShape sh[2];
   for (int p = 0; p < 2; ++p) GAL_TRY(batch_shape(ctx, pl, p, st, &sh[p]));
   GAL_TRY(enqueue_items<float>(ctx, pl.items[0], sh[0], st));
@@ -1271,6 +1379,30 @@ int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_ou
 int gal_set_batch_tuning(gal_ctx* ctx, int enable) {
   if (!ctx) return GAL_E_INVAL;
   ctx->batch_tuning = enable != 0;
+  return GAL_OK;
+}
+
+int gal_set_fft_radix(int device, int real_bytes, int nxy, int row_radix, int col_radix) {
+  if (device < 0 || device >= plans::kDevices || !pow2_size(nxy)) return GAL_E_INVAL;
+  auto ok = [](int r, int dflt, bool alt) { return r == dflt || (alt && r == gal::kAltRadix); };
+  if (real_bytes == 4) {
+    const bool alt = plan_tunable<float>(nxy);
+    if (!ok(row_radix, 16, alt) || !ok(col_radix, 16, alt)) return GAL_E_INVAL;
+    plan_store<float>(device, nxy, row_radix, col_radix, true);
+    return GAL_OK;
+  }
+  if (real_bytes == 8) return row_radix == 8 && col_radix == 8 ? GAL_OK : GAL_E_INVAL;
+  return GAL_E_INVAL;
+}
+
+int gal_get_fft_radix(int device, int real_bytes, int nxy, int* row_radix, int* col_radix) {
+  if (!row_radix || !col_radix || device < 0 || device >= plans::kDevices || !pow2_size(nxy))
+    return GAL_E_INVAL;
+  bool set;
+  if (real_bytes == 4) set = plan_lookup<float>(device, nxy, row_radix, col_radix);
+  else if (real_bytes == 8) set = plan_lookup<double>(device, nxy, row_radix, col_radix);
+  else return GAL_E_INVAL;
+  if (!set) *row_radix = *col_radix = 0;
   return GAL_OK;
 }
 
@@ -1578,3 +1710,9 @@ int gal_chi2_image_host_f64(gal_ctx* ctx, const double* image_host, int nxy, dou
 }
 
 }  // extern "C"
+
+namespace gal {
+void fft_plan_lookup_f32(int device, int nxy, int* rv, int* cv) {
+  plan_lookup<float>(device, nxy, rv, cv);
+}
+}  // namespace gal

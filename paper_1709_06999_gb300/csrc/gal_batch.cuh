@@ -29,12 +29,12 @@ inline int chunk_of(const BatchShape& sh) {
 // rows: the chunk `idx[0..n)` of items, all of length 2^(LG+1), all swept
 // (SWEEP) or all images, all with a beam (BEAM, its tables already computed
 // earlier in the stream) or none
-template <typename T, int LG, bool SWEEP, bool BEAM>
+template <typename T, int LG, bool SWEEP, bool BEAM, int V = FftV<T>::V>
 cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int* err,
                  const BatchShape& sh, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LG, N = 2 * M;
-  using SH = Shape3<T, M, N>;
+  using SH = Shape3<T, M, N, 128, V>;
   Jobs<RowJob<T>, kBatchJobs> jb{};
   for (int k = 0; k < n; ++k) {
     const BatchItem& b = it[idx[k]];
@@ -44,7 +44,7 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
   }
   const C* twc = static_cast<const C*>(tw);
   if constexpr (!SWEEP) {
-    constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs, BEAM>;
+    constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs, BEAM, 128, 2, V>;
     const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
     cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
@@ -59,7 +59,7 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
     if (x < 1) x = 1;
     kern<<<dim3(x, n), SH::threads, smem, st>>>(jb, twc, err);
   } else {
-    constexpr auto kern = row_fft3_kernel<T, LG, false, true, kBatchJobs, BEAM>;
+    constexpr auto kern = row_fft3_kernel<T, LG, false, true, kBatchJobs, BEAM, 128, 2, V>;
     const size_t smem = 128 + (size_t)2 * SH::G * SH::RS * sizeof(C);
     const cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
@@ -86,12 +86,12 @@ cudaError_t rows_full(const BatchItem* it, const int* idx, int n, const void* tw
   else return launch_row_c2c_tma<T, LG, kBatchJobs>(jb, n, sh.row_blocks, false, tw, err, st);
 }
 
-template <typename T, int LG>
+template <typename T, int LG, int V = FftV<T>::V>
 cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = ColShape3<T, N>;
-  constexpr auto kern = col_fft3_kernel<T, LG, kBatchJobs>;
+  using SH = ColShape3<T, N, V>;
+  constexpr auto kern = col_fft3_kernel<T, LG, kBatchJobs, V>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -209,7 +209,7 @@ cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* 
                                  const BatchShape& sh, int* launches, cudaStream_t st) {
   auto pick = [](const BatchItem&) { return true; };
   auto key = [](const BatchItem& b) {
-    return b.N * 8 + (b.full ? 4 : 0) + (b.beam ? 2 : 0) + (b.I ? 1 : 0);
+    return (b.N * 8 + (b.full ? 4 : 0) + (b.beam ? 2 : 0) + (b.I ? 1 : 0)) * 64 + b.radix_row;
   };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
     const int lg = ilog2i(b0.N);
@@ -231,11 +231,17 @@ cudaError_t BatchLaunch<T>::rows(const BatchItem* it, int n, const void* const* 
       if constexpr (LG > 12) {
         return cudaErrorNotSupported;
       } else {
-        if (b0.beam)
-          return b0.I ? batch::rows<T, LG, true, true>(it, idx, m, tw[lg], err, sh, st)
-                      : batch::rows<T, LG, false, true>(it, idx, m, tw[lg], err, sh, st);
-        return b0.I ? batch::rows<T, LG, true, false>(it, idx, m, tw[lg], err, sh, st)
-                    : batch::rows<T, LG, false, false>(it, idx, m, tw[lg], err, sh, st);
+        auto go = [&](auto v_c) {
+          constexpr int VV = decltype(v_c)::value;
+          if (b0.beam)
+            return b0.I ? batch::rows<T, LG, true, true, VV>(it, idx, m, tw[lg], err, sh, st)
+                        : batch::rows<T, LG, false, true, VV>(it, idx, m, tw[lg], err, sh, st);
+          return b0.I ? batch::rows<T, LG, true, false, VV>(it, idx, m, tw[lg], err, sh, st)
+                      : batch::rows<T, LG, false, false, VV>(it, idx, m, tw[lg], err, sh, st);
+        };
+        if constexpr (has_alt_radix<T, (2 << LG)>())
+          if (b0.radix_row == kAltRadix) return go(std::integral_constant<int, kAltRadix>{});
+        return go(std::integral_constant<int, FftV<T>::V>{});
       }
     });
     if (!e) ++*launches;
@@ -247,7 +253,7 @@ template <typename T>
 cudaError_t BatchLaunch<T>::cols(const BatchItem* it, int n, const void* const* tw,
                                  const BatchShape& sh, int* launches, cudaStream_t st) {
   auto pick = [](const BatchItem&) { return true; };
-  auto key = [](const BatchItem& b) { return b.N; };
+  auto key = [](const BatchItem& b) { return b.N * 64 + b.radix_col; };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem& b0) {
     const int lg = ilog2i(b0.N);
     const cudaError_t e = batch::by_lg<T, ilog2c(FftV<T>::V)>(lg, [&](auto L) {
@@ -255,6 +261,8 @@ cudaError_t BatchLaunch<T>::cols(const BatchItem* it, int n, const void* const* 
       if constexpr (LG > col3_max_lg<T>()) {
         return cudaErrorNotSupported;
       } else {
+        if constexpr (has_alt_radix<T, (1 << LG)>())
+          if (b0.radix_col == kAltRadix) return batch::cols<T, LG, kAltRadix>(it, idx, m, tw[lg], st);
         return batch::cols<T, LG>(it, idx, m, tw[lg], st);
       }
     });

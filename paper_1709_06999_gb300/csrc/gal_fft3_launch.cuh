@@ -8,13 +8,13 @@ namespace gal {
 
 // A row pass with a beam follows beam_table_kernel in the stream and is
 // launched as its programmatic dependent (BEAM kernels wait for the tables).
-template <typename T, int LG, bool SWEEP, bool BEAM>
+template <typename T, int LG, bool SWEEP, bool BEAM, int V = FftV<T>::V>
 cudaError_t launch_row3_kern(const Jobs<RowJob<T>, 1>& jb, const cplx_t<T>* twc, int* err,
                              cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LG, N = 2 * M;
-  using SH = Shape3<T, M, N>;
-  constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM>;
+  using SH = Shape3<T, M, N, 128, V>;
+  constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM, 128, 2, V>;
   const size_t smem = 128 + (size_t)(SWEEP ? 2 : 3) * SH::G * SH::RS * sizeof(C);
   cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -31,26 +31,37 @@ cudaError_t launch_row3_kern(const Jobs<RowJob<T>, 1>& jb, const cplx_t<T>* twc,
   return cudaGetLastError();
 }
 
+// the radix-8 float passes exist for image sides up to kAltRadixMaxSide
+template <typename T, int N> constexpr bool has_alt_radix() {
+  return sizeof(T) == 4 && N <= kAltRadixMaxSide && N / 2 >= kAltRadix;
+}
+
 template <typename T, int LG, bool SWEEP>
 cudaError_t launch_row3(const T* image, const T* I, const SweepParams& sp, const void* tw,
                         void* F1, const double* rho2, double S, int* err, const T* beam,
-                        cudaStream_t st) {
+                        cudaStream_t st, int radix) {
   using C = cplx_t<T>;
   const C* twc = static_cast<const C*>(tw);
   Jobs<RowJob<T>, 1> jb;
   jb.j[0] = RowJob<T>{image, I, SWEEP ? sweep_cast<T>(sp) : SweepT<T>{}, static_cast<C*>(F1),
                       rho2, S, beam};
+  if constexpr (has_alt_radix<T, (2 << LG)>()) {
+    if (radix == kAltRadix) {
+      if (beam) return launch_row3_kern<T, LG, SWEEP, true, kAltRadix>(jb, twc, err, st);
+      return launch_row3_kern<T, LG, SWEEP, false, kAltRadix>(jb, twc, err, st);
+    }
+  }
   if (beam) return launch_row3_kern<T, LG, SWEEP, true>(jb, twc, err, st);
   return launch_row3_kern<T, LG, SWEEP, false>(jb, twc, err, st);
 }
 
-template <typename T, int LG>
-cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
-                        int kc_hint, bool full, cudaStream_t st) {
+template <typename T, int LG, int V = FftV<T>::V>
+cudaError_t launch_col3_kern(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
+                             int kc_hint, bool full, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int N = 1 << LG;
-  using SH = ColShape3<T, N>;
-  constexpr auto kern = col_fft3_kernel<T, LG, 1>;
+  using SH = ColShape3<T, N, V>;
+  constexpr auto kern = col_fft3_kernel<T, LG, 1, V>;
   const size_t smem = (size_t)2 * SH::G * SH::RS * sizeof(C);
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
@@ -66,17 +77,27 @@ cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* 
 }
 
 template <typename T, int LG>
+cudaError_t launch_col3(const void* F1, void* Gw, const void* tw, const double* rho2, double S,
+                        int kc_hint, bool full, cudaStream_t st, int radix) {
+  if constexpr (has_alt_radix<T, (1 << LG)>()) {
+    if (radix == kAltRadix)
+      return launch_col3_kern<T, LG, kAltRadix>(F1, Gw, tw, rho2, S, kc_hint, full, st);
+  }
+  return launch_col3_kern<T, LG>(F1, Gw, tw, rho2, S, kc_hint, full, st);
+}
+
+template <typename T, int LG>
 cudaError_t row3_switch(int lg, const T* image, const T* I, const SweepParams& sp,
                         const void* tw, void* F1, const double* rho2, double S, int* err,
-                        const T* beam, cudaStream_t st) {
+                        const T* beam, cudaStream_t st, int radix) {
   if constexpr (LG > 12) {
     return cudaErrorNotSupported;
   } else {
     if (lg == LG) {
-      if (I) return launch_row3<T, LG, true>(image, I, sp, tw, F1, rho2, S, err, beam, st);
-      return launch_row3<T, LG, false>(image, I, sp, tw, F1, rho2, S, err, beam, st);
+      if (I) return launch_row3<T, LG, true>(image, I, sp, tw, F1, rho2, S, err, beam, st, radix);
+      return launch_row3<T, LG, false>(image, I, sp, tw, F1, rho2, S, err, beam, st, radix);
     }
-    return row3_switch<T, LG + 1>(lg, image, I, sp, tw, F1, rho2, S, err, beam, st);
+    return row3_switch<T, LG + 1>(lg, image, I, sp, tw, F1, rho2, S, err, beam, st, radix);
   }
 }
 
@@ -86,12 +107,12 @@ template <typename T> constexpr int col3_max_lg() { return sizeof(T) == 4 ? 13 :
 
 template <typename T, int LG>
 cudaError_t col3_switch(int lg, const void* F1, void* Gw, const void* tw, const double* rho2,
-                        double S, int kc_hint, bool full, cudaStream_t st) {
+                        double S, int kc_hint, bool full, cudaStream_t st, int radix) {
   if constexpr (LG > col3_max_lg<T>()) {
     return cudaErrorNotSupported;
   } else {
-    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, full, st);
-    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, full, st);
+    if (lg == LG) return launch_col3<T, LG>(F1, Gw, tw, rho2, S, kc_hint, full, st, radix);
+    return col3_switch<T, LG + 1>(lg, F1, Gw, tw, rho2, S, kc_hint, full, st, radix);
   }
 }
 
@@ -104,16 +125,16 @@ inline int ilog2i(int n) {
 template <typename T>
 cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
                      void* F1, const double* rho2, double S, int* err, const T* beam,
-                     cudaStream_t st) {
+                     cudaStream_t st, int radix) {
   constexpr int LG0 = ilog2c(FftV<T>::V);
-  return row3_switch<T, LG0>(ilog2i(N / 2), image, I, sp, tw, F1, rho2, S, err, beam, st);
+  return row3_switch<T, LG0>(ilog2i(N / 2), image, I, sp, tw, F1, rho2, S, err, beam, st, radix);
 }
 
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, bool full, cudaStream_t st) {
+                     int kc_hint, bool full, cudaStream_t st, int radix) {
   constexpr int LG0 = ilog2c(FftV<T>::V);
-  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, full, st);
+  return col3_switch<T, LG0>(ilog2i(N), F1, Gw, tw, rho2, S, kc_hint, full, st, radix);
 }
 
 }  // namespace gal

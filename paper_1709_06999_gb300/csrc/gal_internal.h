@@ -65,10 +65,11 @@ template <typename T> struct Launch {
   static cudaError_t sweep(const T* I, const SweepParams& sp, int N, T* img, int blocks,
                            cudaStream_t st);
   // err: bit 2 is set if a staged copy's wait timed out (never expected);
-  // beam: primary-beam tables of beam_table (null: no beam)
+  // beam: primary-beam tables of beam_table (null: no beam); radix: values per
+  // thread of the compile-time FFT stages (0: the default, fft_radix_default)
   static cudaError_t row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                               const void* tw, void* F1, const double* rho2, double S, int* err,
-                              const T* beam, cudaStream_t st);
+                              const T* beam, cudaStream_t st, int radix = 0);
   // primary-beam tables (2 N values) for a beam of FWHM fwhm > 0 on the
   // pointing centre, seen from a model moved by (dRA, dDec) at position angle PA
   static cudaError_t beam_table(T* tab, int N, double dxy, double fwhm, double dRA, double dDec,
@@ -77,7 +78,7 @@ template <typename T> struct Launch {
   // full-plane window of full_cols (lengths of the compile-time passes only)
   static cudaError_t col_pass(const void* F1, void* Gw, int N, const void* tw,
                               const double* rho2, double S, int kc_hint, bool full,
-                              cudaStream_t st);
+                              cudaStream_t st, int radix = 0);
   // ms: multi-source offsets (null: the single offset of gp)
   static cudaError_t gather(const void* Gw, const GatherParams& gp, const double* rho2,
                             const T* u, const T* v, const T* re, const T* im, const T* w,
@@ -108,6 +109,18 @@ template <typename T> struct Plane {
 // parameters: 32 gather jobs take about 8 KB of the 32 KB parameter space).
 constexpr int kBatchJobs = 32;
 
+// FFT radix (values per thread of every stage but the last) of the
+// compile-time row and column passes.  Float transforms run at radix 16; for
+// image sides up to kAltRadixMaxSide the radix-8 passes exist too, and the
+// FFT plan (a per-device choice per side, see gal_set_fft_radix) says which
+// of the two a call uses.  Double transforms always run at radix 8.
+template <typename T> constexpr int fft_radix_default() { return sizeof(T) == 4 ? 16 : 8; }
+constexpr int kAltRadix = 8;
+constexpr int kAltRadixMaxSide = 512;
+// the FFT plan of a float32 side on `device` if one is fixed, the defaults
+// otherwise (fixes nothing; for callers without a context)
+void fft_plan_lookup_f32(int device, int nxy, int* rv, int* cv);
+
 // One request of a batch, planned by the C-ABI layer (host values and device
 // pointers).  Exactly one of image / I is set.
 struct BatchItem {
@@ -133,6 +146,8 @@ struct BatchItem {
   BeamParams bp;       // their parameters
   bool full;           // full-plane spectrum (complex-to-complex rows, no fold)
   int ncol;            // window columns: Kc, or full_cols(...).W for the full plane
+  int radix_row;       // FFT plan of side N: row and column pass radix (0: default)
+  int radix_col;
 };
 
 // Launch shape of the batched passes.  Results do not depend on it (every
@@ -164,9 +179,9 @@ template <typename T> struct BatchLaunch {
 template <typename T>
 cudaError_t row_fft3(const T* image, const T* I, const SweepParams& sp, int N, const void* tw,
                      void* F1, const double* rho2, double S, int* err, const T* beam,
-                     cudaStream_t st);
+                     cudaStream_t st, int radix);
 template <typename T>
 cudaError_t col_fft3(const void* F1, void* Gw, int N, const void* tw, const double* rho2, double S,
-                     int kc_hint, bool full, cudaStream_t st);
+                     int kc_hint, bool full, cudaStream_t st, int radix);
 
 }  // namespace gal

@@ -1710,12 +1710,12 @@ cudaError_t Launch<T>::sweep(const T* I, const SweepParams& sp, int N, T* img, i
 template <typename T>
 cudaError_t Launch<T>::row_pass(const T* image, const T* I, const SweepParams& sp, int N,
                                 const void* tw, void* F1, const double* rho2, double S, int* err,
-                                const T* beam, cudaStream_t st) {
+                                const T* beam, cudaStream_t st, int radix) {
   using C = cplx_t<T>;
   const int M = N / 2;
   const bool al16 = I || (reinterpret_cast<uintptr_t>(image) & 15u) == 0;
   if (M >= FftV<T>::V && al16) {
-    const cudaError_t e = row_fft3<T>(image, I, sp, N, tw, F1, rho2, S, err, beam, st);
+    const cudaError_t e = row_fft3<T>(image, I, sp, N, tw, F1, rho2, S, err, beam, st, radix);
     if (e != cudaErrorNotSupported) return e;
   }
   const C* twc = static_cast<const C*>(tw);
@@ -1749,10 +1749,10 @@ cudaError_t Launch<T>::beam_table(T* tab, int N, double dxy, double fwhm, double
 template <typename T>
 cudaError_t Launch<T>::col_pass(const void* F1, void* Gw, int N, const void* tw,
                                 const double* rho2, double S, int kc_hint, bool full,
-                                cudaStream_t st) {
+                                cudaStream_t st, int radix) {
   using C = cplx_t<T>;
   if (N >= FftV<T>::V) {
-    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, full, st);
+    const cudaError_t e = col_fft3<T>(F1, Gw, N, tw, rho2, S, kc_hint, full, st, radix);
     if (e != cudaErrorNotSupported) return e;
   }
   if (full) return cudaErrorNotSupported;  // the generic pass keeps the half plane only

@@ -72,6 +72,7 @@ int setup_current_device(DeviceSetup** out) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+
 // After the gather: a bounded wait of the row pass that gave up (the error
 // word is non-zero) left the spectrum incomplete, so the result is replaced by
 // NaN.  With no context there is no gal_check to report it; the NaN does.
@@ -118,9 +119,13 @@ extern "C" int gal_chi2_image_noalloc_f32(const float* image, int nxy, double dx
     return GAL_E_CUDA;
   const double S = (double)nxy * dxy;
   gal::SweepParams none{};
-  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, nullptr, cs) != cudaSuccess)
+  int dev = 0, rv = 0, cv = 0;
+  cudaGetDevice(&dev);
+  gal::fft_plan_lookup_f32(dev, nxy, &rv, &cv);
+  if (gal::Launch<float>::row_pass(image, nullptr, none, nxy, tw, F1, rho2, S, err, nullptr, cs,
+                                   rv) != cudaSuccess)
     return GAL_E_CUDA;
-  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, 0, false, cs) != cudaSuccess)
+  if (gal::Launch<float>::col_pass(F1, Gw, nxy, tw, rho2, S, 0, false, cs, cv) != cudaSuccess)
     return GAL_E_CUDA;
   gal::GatherParams gp;
   gp.cpa = std::cos(PA);

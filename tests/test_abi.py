@@ -102,3 +102,24 @@ def test_struct_layouts_match_c(tmp_path):
         assert int(got[name]) == ct.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_fft_radix_plan_validation():
+    """The FFT plan calls are host-side: the set of valid radices per side and
+    precision, and that a plan set is read back (no GPU needed)."""
+    from paper_1709_06999_gb300 import GalError, get_fft_radix, set_fft_radix
+    set_fft_radix(5, "float32", 256, 8, 16)
+    assert get_fft_radix(5, "float32", 256) == (8, 16)
+    set_fft_radix(5, "float32", 256, 16, 8)
+    assert get_fft_radix(5, "float32", 256) == (16, 8)
+    assert get_fft_radix(5, "float32", 128) == (0, 0)          # not fixed yet
+    assert get_fft_radix(5, "float32", 4096) == (16, 16)       # one radix only
+    assert get_fft_radix(5, "float64", 256) == (8, 8)
+    for bad in ((5, "float32", 1024, 8, 16),    # radix 8 only up to 512
+                (5, "float32", 256, 4, 16),     # no radix 4
+                (5, "float32", 16, 8, 8),       # below 32
+                (5, "float32", 300, 16, 16),    # not a power of two
+                (5, "float64", 256, 16, 8),     # float64 runs at 8
+                (-1, "float32", 256, 16, 16)):
+        with pytest.raises(GalError):
+            set_fft_radix(*bad)
