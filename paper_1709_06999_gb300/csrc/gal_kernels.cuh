@@ -812,21 +812,6 @@ __device__ __forceinline__ float prod_hi_lo(float a, ff b, float& lo) {
   return hi;
 }
 
-// cell and fraction of a position given as hi + lo; the cell is floor(pos),
-// the fraction pos - cell in [0, 1)
-__device__ __forceinline__ void split_cell(float h, float l, float& cell, float& frac) {
-  cell = floorf(h);
-  frac = (h - cell) + l;
-  if (frac < 0.f) {
-    cell -= 1.f;
-    frac += 1.f;
-  } else if (frac >= 1.f) {
-    cell += 1.f;
-    frac -= 1.f;
-  }
-  cell = fminf(fmaxf(cell, -32768.f), 32768.f);
-}
-
 // a window node from global memory (read-only cache) or from shared memory
 template <bool SMEM, typename C> __device__ __forceinline__ C ld_node(const C* p) {
   if constexpr (SMEM) return *p;
@@ -862,20 +847,23 @@ __device__ __forceinline__ float2 sample_point(const cplx_t<float>* __restrict__
   float yh = ya + yb;
   t = yh - ya;
   float yl = ((ya - (yh - t)) + (yb - t)) + (yae + ybe);
-  // Hermitian fold (half spectrum only): use (-u', -v') and conjugate
-  const bool neg = !FULL && xh < 0.f;
+  // Hermitian fold (half spectrum only): use (-u', -v') and conjugate.  The
+  // sign is that of the whole position hi + lo (hi alone is 0 when the two
+  // products cancel, with the position in lo).
+  const bool neg = !FULL && xh + xl < 0.f;
   if (neg) {
     xh = -xh;
     xl = -xl;
     yh = -yh;
     yl = -yl;
   }
-  // cell = floor(hi); fraction = (hi - cell) + lo.  When hi sits within |lo|
-  // of an integer the fraction leaves [0, 1] by at most |lo| (one ulp of hi),
-  // a linear extrapolation across the node that equals the neighbouring
-  // cell's interpolation to that order.  Every cell path computes the
-  // fraction this way, so the sampling and chi-square kernels agree bit for bit.
-  const float cf = floorf(xh), rf = floorf(yh);
+  // The cell of a position hi + lo is floor(hi + lo), taken from the sum
+  // rounded down (exactly the floor of the exact sum; floor(hi) alone is one
+  // cell off when lo carries the position across a node, and the bilinear
+  // interpolant has a kink there).  The fraction (hi - cell) + lo is then
+  // in [0, 1], with one rounding.  Every cell path computes both this way, so
+  // the sampling and chi-square kernels agree bit for bit.
+  const float cf = floorf(__fadd_rd(xh, xl)), rf = floorf(__fadd_rd(yh, yl));
   float fu = (xh - cf) + xl;
   float fv = (yh - rf) + yl;
   int c = FULL ? (int)fmaxf(fminf(cf, 32768.f), -32768.f) + w.cofs : (int)fminf(cf, 32768.f);
@@ -998,11 +986,11 @@ __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const W
   // positions are grid offsets (|.| <= 8192), so the FMA-pipe floor applies;
   // non-finite input yields an arbitrary cell, clamped below, and NaN through
   // the phase
+  // cell = floor(hi + lo) from the sum rounded down, fraction (hi - cell) +
+  // lo, as in sample_point and cell_pair_pruned (same values, bit for bit)
   float cf, rf;
-  int c = floor_fma(xh, cf) + (FULL ? w.cofs : 0);
-  int r = floor_fma(yh, rf) + w.rofs;
-  // fraction as in sample_point: (hi - cell) + lo, not clamped, so that this
-  // path and cell_pair_pruned give the same value for every in-window point
+  int c = floor_fma(__fadd_rd(xh, xl), cf) + (FULL ? w.cofs : 0);
+  int r = floor_fma(__fadd_rd(yh, yl), rf) + w.rofs;
   float fu = (xh - cf) + xl;
   float fv = (yh - rf) + yl;
   if constexpr (EDGE) {
@@ -1038,9 +1026,9 @@ __device__ __forceinline__ void cell_fetch(const float2* __restrict__ G, const W
 
 // Both points' cells in a pruned window (no point can reach its edge), from
 // the folded positions x = xh + xl, y = yh + yl (grid offsets, |.| < 2^22):
-// floor(h) + 1.5 2^23 is h + 1.5 2^23 rounded down (one add per lane pair),
-// whose low mantissa bits are the integer floor; the fraction (h - floor h)
-// is exact, plus the low part.  Non-finite input gives an arbitrary node
+// the cell is floor(h + l), which is (h + l rounded down) + 1.5 2^23 rounded
+// down (two adds per lane pair), whose low mantissa bits are the integer
+// floor; the fraction (h - floor) is exact, plus the low part.  Non-finite input gives an arbitrary node
 // index, clamped so every read stays in the window (its result is NaN
 // through the phase).
 template <bool SMEM, bool FULL = false>
@@ -1048,7 +1036,8 @@ __device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, c
                                                  float2 xh, float2 xl, float2 yh, float2 yl,
                                                  float2 m1, float2& A0, float2& A1) {
   const float2 mg = make_float2(kMagic, kMagic), nmg = make_float2(-kMagic, -kMagic);
-  const float2 tx = add2_rd(xh, mg), ty = add2_rd(yh, mg);
+  // floor(hi + lo): the sum rounded down, then rounded down to an integer
+  const float2 tx = add2_rd(add2_rd(xh, xl), mg), ty = add2_rd(add2_rd(yh, yl), mg);
   const float2 fu = add2(fma2(add2(tx, nmg), m1, xh), xl);
   const float2 fv = add2(fma2(add2(ty, nmg), m1, yh), yl);
   constexpr int kMagicBits = 0x4B400000;  // bit pattern of 1.5 2^23
@@ -1132,8 +1121,9 @@ __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const 
       cell_pair_pruned<SMEM, true>(G, w, xh2, xl2, yh2, yl2, k.m1, A0, A1);
     }
   } else {
-    // Hermitian fold per lane
-    const bool n0 = xh2.x < 0.f, n1 = xh2.y < 0.f;
+    // Hermitian fold per lane, on the sign of the whole position hi + lo
+    const float2 xs = add2(xh2, xl2);
+    const bool n0 = xs.x < 0.f, n1 = xs.y < 0.f;
     const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
     const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
     if constexpr (EDGE) {
