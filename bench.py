@@ -40,7 +40,7 @@ NXY, M_UV = 4096, 5_000_000
 L2_FLUSH_BYTES = 256 << 20
 STAGES = ["uv_extent", "row_fft", "col_fft", "gather_chi2"]
 # kernels launched for this workload (template arguments as ncu prints them)
-KERNELS = {1: "row_fft3_kernel<float, 11, 1, 0, 1, 0, 128, 2, 16>",
+KERNELS = {1: "row_fft3_ldg_kernel<1, 0>",
            2: "col_fft3_kernel<float, 12, 1, 16>", 3: "gather_kernel<float, 1, 1, 0, 1, 0, 0>"}
 # the full-plane (complex-to-complex) spectrum path
 KERNELS_FULL = {1: "row_c2c_tma_kernel<float, 12, 1>", 2: "col_fft3_kernel<float, 12, 1, 16>",

@@ -43,7 +43,16 @@ cudaError_t rows(const BatchItem* it, const int* idx, int n, const void* tw, int
                         b.S, BEAM ? static_cast<const T*>(b.beam) : nullptr};
   }
   const C* twc = static_cast<const C*>(tw);
-  if constexpr (!SWEEP) {
+  if constexpr (row_ldg_shape<T, LG, SWEEP, V>()) {
+    // the same kernel as single calls of this length (bitwise equal results)
+    constexpr auto kern = row_fft3_ldg_kernel<kBatchJobs, BEAM>;
+    const cudaError_t e = ensure_smem_attr<kern>(RowLdgShape::smem);
+    if (e) return e;
+    int x = row_ldg_grid<kern>(n) * (sh.row_blocks < 1 ? 1 : sh.row_blocks);
+    if (x > RowLdgShape::N) x = RowLdgShape::N;
+    if (x < 1) return cudaErrorInvalidConfiguration;
+    kern<<<dim3(x, n), RowLdgShape::TT, RowLdgShape::smem, st>>>(jb, twc);
+  } else if constexpr (!SWEEP) {
     constexpr auto kern = row_fft3_kernel<T, LG, true, false, kBatchJobs, BEAM, 128, 2, V>;
     const size_t smem = 128 + (size_t)3 * SH::G * SH::RS * sizeof(C);
     cudaError_t e = ensure_smem_attr<kern>(smem);

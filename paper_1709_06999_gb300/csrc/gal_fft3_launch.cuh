@@ -2,9 +2,28 @@
 // instantiation per transform length, chosen by a switch on log2 of it.
 #pragma once
 
+#include <type_traits>
+
 #include "gal_kernels.cuh"
 
 namespace gal {
+
+// Image rows of the one length row_fft3_ldg_kernel serves (float, 4096
+// pixels, radix 16) take that kernel, in single calls and batches alike.
+template <typename T, int LG, bool SWEEP, int V> constexpr bool row_ldg_shape() {
+  return std::is_same<T, float>::value && !SWEEP && LG == kRowLdgLG && V == 16;
+}
+// its persistent grid: the resident blocks of the device, shared by the
+// `n` requests of a launch (grid row y = request), at most one row each
+template <auto Kern> int row_ldg_grid(int n) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kern, RowLdgShape::TT,
+                                                    RowLdgShape::smem) != cudaSuccess)
+    return 0;
+  if (per_sm < 1) per_sm = 1;
+  int x = (per_sm * current_device_sms() + n - 1) / n;
+  return x > RowLdgShape::N ? RowLdgShape::N : x;
+}
 
 // A row pass with a beam follows beam_table_kernel in the stream and is
 // launched as its programmatic dependent (BEAM kernels wait for the tables).
@@ -13,6 +32,18 @@ cudaError_t launch_row3_kern(const Jobs<RowJob<T>, 1>& jb, const cplx_t<T>* twc,
                              cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LG, N = 2 * M;
+  if constexpr (row_ldg_shape<T, LG, SWEEP, V>()) {  // float rows of 4096 pixels
+    constexpr auto kern = row_fft3_ldg_kernel<1, BEAM>;
+    cudaError_t e = ensure_smem_attr<kern>(RowLdgShape::smem);
+    if (e) return e;
+    const int grid = row_ldg_grid<kern>(1);
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    if constexpr (BEAM)
+      return launch_dependent(kern, dim3(grid), dim3(RowLdgShape::TT), RowLdgShape::smem, st, jb, twc);
+    kern<<<grid, RowLdgShape::TT, RowLdgShape::smem, st>>>(jb, twc);
+    return cudaGetLastError();
+  }
+  (void)err;
   using SH = Shape3<T, M, N, 128, V>;
   constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM, 128, 2, V>;
   const size_t smem = 128 + (size_t)(SWEEP ? 2 : 3) * SH::G * SH::RS * sizeof(C);

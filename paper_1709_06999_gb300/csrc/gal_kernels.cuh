@@ -540,6 +540,176 @@ row_fft3_kernel(const __grid_constant__ Jobs<RowJob<T>, K> jobs, const cplx_t<T>
   }
 }
 
+// ---------------------------------------------------------------------------
+// Row pass of the float 4096-wide image (M = 2048 complex points, stages
+// 16 x 16 x 8), the shape of the large single-image evaluation.  Differences
+// from row_fft3_kernel:
+//  * rows are read with plain 8-byte loads straight into the stage-0
+//    register layout, the next row in flight while this one is transformed
+//    (the bulk-copy ring alone needs about as long as the whole pass);
+//  * when the kept window has at most 64 columns, the pruned radix-8 last
+//    stage runs in registers and warp shuffles: stage 1 gives thread
+//    (k, blk) = (t >> 3, t & 7) the butterfly 16 blk + k, whose outputs are
+//    Y[256 blk + k + 16 r']; the 8 lanes of one k hold every Y that the
+//    outputs at in-block positions p = k (mod 16) need, and
+//      X[p + 256 s] = sum_blk Y[p + 256 blk] W_2048^(blk p) W_8^(blk s)
+//    is a sum over those 8 lanes (transpose-reduce: 7 complex shuffles per
+//    lane).  Output slots: s = 0 for r' = 0..3 (X[j], j < 64) and s = 7 for
+//    r' = 12..15 (X[2048 - j], j = 1..64).  The stage 0 -> 1 exchange goes
+//    through an unpadded buffer with element 16 a + c at
+//    16 a + ((c + 2a + (a >> 3)) & 15), free of bank conflicts for both the
+//    stage-0 stores and the remapped stage-1 loads.
+//  * otherwise (wider windows) each row takes row_fft3_kernel's transform.
+// Every request of a launch (grid row y) takes the same branch for all its
+// rows, and single calls and batches use this kernel alike, so their results
+// stay bitwise equal.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int swz16(int a, int c) { return 16 * a + ((c + 2 * a + (a >> 3)) & 15); }
+
+constexpr int kRowLdgLG = 11;      // the one transform length of row_fft3_ldg_kernel
+constexpr int kRowLdgMaxKc = 64;   // widest window of its register last stage
+constexpr int kRowLdgBlocks = 3;   // resident blocks per SM (168 registers each)
+
+struct RowLdgShape {
+  using P = P3<(1 << kRowLdgLG), 16>;
+  static constexpr int M = 1 << kRowLdgLG, N = 2 * M, V = 16, TT = P::T;
+  static constexpr int RS = (P::padded * 8 + 15) / 16 * 16 / 8;
+  static constexpr int kZ = 2 * kRowLdgMaxKc + 1;  // Z[j] for j < 64, Z[M - j] for j = 1..64
+  static constexpr size_t smem = (size_t)(2 * RS + kZ) * sizeof(float2);
+};
+
+template <int K, bool BEAM = false>
+__global__ void __launch_bounds__(RowLdgShape::TT, kRowLdgBlocks)
+row_fft3_ldg_kernel(const __grid_constant__ Jobs<RowJob<float>, K> jobs, const float2* __restrict__ tw) {
+  using C = float2;
+  using SH = RowLdgShape;
+  using P = SH::P;
+  constexpr int M = SH::M, N = SH::N, V = SH::V, TT = SH::TT, RS = SH::RS;
+  static_assert(P::nstage == 3 && P::rlast == 8 && P::Nsl == 256 && TT == 128, "shape");
+  grid_dep_launch();  // the column pass may be scheduled as our blocks retire
+  const RowJob<float>& jb = jobs.j[K == 1 ? 0 : blockIdx.y];
+  const float* __restrict__ image = jb.image;
+  const float* __restrict__ beam = BEAM ? jb.beam : nullptr;
+  C* __restrict__ F1 = jb.F1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + RS;
+  C* zlo = B + RS;                  // Z[j], j < 64
+  C* zhi = zlo + kRowLdgMaxKc;      // Z[M - j] at index j, j = 1..64
+  const int t = threadIdx.x;
+  const Bounds bd = block_bounds(jb.rho2, jb.S, N);
+  const bool pruned = bd.Kc <= P::Nsl;
+  const bool fast = bd.Kc <= kRowLdgMaxKc;  // uniform over the request
+  // fast path: butterfly 16 blk + k of stage 1, twiddles of both stages
+  const int k = t >> 3, blk = t & 7;
+  C tw1[V - 1];
+  C twl[8];
+  C wj = mkc(0.f, 0.f);
+  if (fast) {
+#pragma unroll
+    for (int r = 1; r < V; ++r) tw1[r - 1] = __ldg(tw + 16 * r * k);  // W_256^(r k)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = k + 16 * (i < 4 ? i : 8 + i);
+      const int e = (blk * p + (i < 4 ? 0 : 256 * 7 * blk)) & (M - 1);
+      twl[i] = __ldg(tw + 2 * e);  // W_2048^(blk p) W_8^(blk s)
+    }
+    if (t < bd.Kc) wj = __ldg(tw + t);
+  } else {
+    load_tw1<M, V, 2>(tw1, t, tw);
+  }
+  C twp[V];
+  if (!fast && pruned && t < bd.Kc) {
+    load_twp<M, V, 2>(twp, t, tw);
+    wj = __ldg(tw + t);
+  }
+  auto load_row = [&](C (&x)[V], int row) {
+    // row `row` of fftshift(image): image row (row + N/2) mod N, halves swapped
+    const float* src = image + (size_t)((row + M) & (N - 1)) * N;
+#pragma unroll
+    for (int r = 0; r < V; ++r)
+      x[r] = __ldcs(reinterpret_cast<const C*>(src + ((2 * (t + r * TT) + M) & (N - 1))));
+  };
+  auto sync = [] { __syncthreads(); };
+  int row = blockIdx.x;
+  C v[V];
+  if (row < N) load_row(v, row);
+  if constexpr (BEAM) grid_dep_wait();  // the beam tables
+  for (; row < N; row += gridDim.x) {
+    const int nrow = row + gridDim.x;
+    C nx[V];
+    if (nrow < N) load_row(nx, nrow);
+    if constexpr (BEAM) {
+#pragma unroll
+      for (int r = 0; r < V; ++r) v[r] = beam_pair(v[r], beam, N, row, t + r * TT);
+    }
+    C* out = F1 + row;  // column-major: bin j of this row at out[j N]
+    if (fast) {
+      // stage 0 (radix 16) into the swizzled buffer
+      bflyR<V>(v);
+#pragma unroll
+      for (int r = 0; r < V; ++r) A[swz16(t, r)] = v[bfly_out<V>(r)];
+      __syncthreads();
+      // stage 1: butterfly b = 16 blk + k, inputs b + 128 r
+#pragma unroll
+      for (int r = 0; r < V; ++r) v[r] = A[swz16(blk + 8 * r, k)];
+#pragma unroll
+      for (int r = 1; r < V; ++r) v[r] = cmul(v[r], tw1[r - 1]);
+      bflyR<V>(v);
+      // last stage over the 8 lanes of this k
+      C x[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) x[i] = cmul(v[bfly_out<V>(i < 4 ? i : 8 + i)], twl[i]);
+      auto xs = [](C a, int m) {
+        return mkc(__shfl_xor_sync(0xffffffffu, a.x, m), __shfl_xor_sync(0xffffffffu, a.y, m));
+      };
+      const bool b2 = blk & 4, b1 = blk & 2, b0 = blk & 1;
+      C y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) y[q] = cadd(b2 ? x[q + 4] : x[q], xs(b2 ? x[q] : x[q + 4], 4));
+      C z2[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) z2[q] = cadd(b1 ? y[q + 2] : y[q], xs(b1 ? y[q] : y[q + 2], 2));
+      const C zz = cadd(b0 ? z2[1] : z2[0], xs(b0 ? z2[0] : z2[1], 1));
+      // lane blk now holds output slot blk
+      if (blk < 4) zlo[k + 16 * blk] = zz;
+      else zhi[256 - (k + 16 * (8 + blk))] = zz;
+      __syncthreads();
+      if (t < bd.Kc) {
+        const C zj = zlo[t];
+        out[(size_t)t * N] = r2c_unpack(zj, t == 0 ? zj : zhi[t], wj);
+      }
+    } else {
+      Head3<M, V, 2, 0>::run(v, A, B, t, tw, tw1, sync);
+      C* in = last_input<M, V>(A, B);
+      if (pruned) {
+        for (int j = t; j < bd.Kc; j += TT) {
+          C zj, zmj;
+          if (bd.Kc <= TT) {
+            pruned_pair3<M, V>(in, j, twp, zj, zmj);
+            out[(size_t)j * N] = r2c_unpack(zj, zmj, wj);
+          } else {
+            C tj[V];
+            load_twp<M, V, 2>(tj, j, tw);
+            pruned_pair3<M, V>(in, j, tj, zj, zmj);
+            out[(size_t)j * N] = r2c_unpack(zj, zmj, __ldg(tw + j));
+          }
+        }
+      } else {
+        last_full<M, V, 2>(v, in, t, tw);
+        C* o = in == A ? B : A;
+        store_full<M, V>(v, o, t);
+        __syncthreads();
+        for (int q = t; q < bd.Kc; q += TT)
+          out[(size_t)q * N] = r2c_unpack(o[pad3<V>(q & (M - 1))], o[pad3<V>((M - q) & (M - 1))], __ldg(tw + q));
+      }
+      __syncthreads();  // every read of A and B is done before the next row
+    }
+#pragma unroll
+    for (int r = 0; r < V; ++r) v[r] = nx[r];
+  }
+}
+
 // Column pass: for each kept column c < Kc (blocks loop over column groups),
 // the complex FFT of length N down column c of F1 (contiguous); output row r
 // of the v-shifted spectrum holds kv = (r + N/2) mod N, and rows r0 ..
