@@ -1380,28 +1380,38 @@ struct AccF {  // Kahan: s holds the sum, c the negated lost low-order part
     c = (t - s) - y;
     s = t;
   }
-  // Block total (valid in thread 0): float-float tree inside each warp, FP64
-  // across warps, so that no per-thread FP64 arithmetic is issued.
+  // Block total (valid in thread 0): a float-float tree inside each warp and
+  // across the warps, converted to FP64 once.  GB300 issues FP64 at a small
+  // fraction of the FP32 rate, and a dependent FP64 tree across 16 warps
+  // added about 1 us to the end of every block; the float-float sums carry
+  // about 48 significant bits.  The sum over blocks stays FP64.
   __device__ __forceinline__ double block_total(double* ws) const {
+    auto warp_tree = [](ff a) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ff b;
+        b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+        a = ff_add(a, b);
+      }
+      return a;
+    };
     ff a;
     a.hi = s;
     a.lo = -c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      ff b;
-      b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
-      b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
-      a = ff_add(a, b);
-    }
+    a = warp_tree(a);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* wf = reinterpret_cast<float2*>(ws);  // 32 doubles hold 32 float pairs
     __syncthreads();
-    if (lane == 0) ws[warp] = (double)a.hi + (double)a.lo;
+    if (lane == 0) wf[warp] = make_float2(a.hi, a.lo);
     __syncthreads();
     double x = 0.0;
     if (warp == 0) {
-      x = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      const float2 w = lane < (int)(blockDim.x >> 5) ? wf[lane] : make_float2(0.f, 0.f);
+      a.hi = w.x;
+      a.lo = w.y;
+      a = warp_tree(a);
+      x = (double)a.hi + (double)a.lo;
     }
     return x;
   }
@@ -1692,9 +1702,17 @@ gather_kernel(const __grid_constant__ Jobs<GatherJob<T>, K> jobs, int smem_nodes
     __syncthreads();
     if (last) {
       __threadfence();
-      AccD a;
-      for (int b = threadIdx.x; b < nvb; b += blockDim.x) a.add(__ldcg(partials + b));
-      const double tot = block_sum(a.value(), ws);
+      // fixed order: thread i compensates partials i, i + blockDim.x, ...
+      // (a single value is taken as it is, the same sum without FP64 work)
+      double x;
+      if (nvb <= (int)blockDim.x) {
+        x = threadIdx.x < nvb ? __ldcg(partials + threadIdx.x) : 0.0;
+      } else {
+        AccD a;
+        for (int b = threadIdx.x; b < nvb; b += blockDim.x) a.add(__ldcg(partials + b));
+        x = a.value();
+      }
+      const double tot = block_sum(x, ws);
       if (threadIdx.x == 0) {
         *chi2_out = tot;
         *counter = 0u;
