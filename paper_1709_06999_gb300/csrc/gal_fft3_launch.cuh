@@ -42,24 +42,25 @@ cudaError_t launch_row3_kern(const Jobs<RowJob<T>, 1>& jb, const cplx_t<T>* twc,
       return launch_dependent(kern, dim3(grid), dim3(RowLdgShape::TT), RowLdgShape::smem, st, jb, twc);
     kern<<<grid, RowLdgShape::TT, RowLdgShape::smem, st>>>(jb, twc);
     return cudaGetLastError();
-  }
-  (void)err;
-  using SH = Shape3<T, M, N, 128, V>;
-  constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM, 128, 2, V>;
-  const size_t smem = 128 + (size_t)(SWEEP ? 2 : 3) * SH::G * SH::RS * sizeof(C);
-  cudaError_t e = ensure_smem_attr<kern>(smem);
-  if (e) return e;
-  int grid = N / SH::G;
-  if constexpr (!SWEEP) {  // persistent blocks over the TMA row ring
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+  } else {
+    using SH = Shape3<T, M, N, 128, V>;
+    constexpr auto kern = row_fft3_kernel<T, LG, !SWEEP, SWEEP, 1, BEAM, 128, 2, V>;
+    const size_t smem = 128 + (size_t)(SWEEP ? 2 : 3) * SH::G * SH::RS * sizeof(C);
+    cudaError_t e = ensure_smem_attr<kern>(smem);
     if (e) return e;
-    if (per_sm < 1) per_sm = 1;
-    if (grid > per_sm * current_device_sms()) grid = per_sm * current_device_sms();
+    int grid = N / SH::G;
+    if constexpr (!SWEEP) {  // persistent blocks over the TMA row ring
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::threads, smem);
+      if (e) return e;
+      if (per_sm < 1) per_sm = 1;
+      if (grid > per_sm * current_device_sms()) grid = per_sm * current_device_sms();
+    }
+    if constexpr (BEAM)
+      return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb, twc, err);
+    kern<<<grid, SH::threads, smem, st>>>(jb, twc, err);
+    return cudaGetLastError();
   }
-  if constexpr (BEAM) return launch_dependent(kern, dim3(grid), dim3(SH::threads), smem, st, jb, twc, err);
-  kern<<<grid, SH::threads, smem, st>>>(jb, twc, err);
-  return cudaGetLastError();
 }
 
 // the radix-8 float passes exist for image sides up to kAltRadixMaxSide
