@@ -685,7 +685,8 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200)
 
 def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
     """Spectral cube (128 Keplerian channels, nxy in {512, 1024, 2048}, M_c in
-    [1e5, 2e6]) and 64 ring-profile walkers (nxy 1024, M 1e6 shared): one
+    [1e5, 2e6]), 64 ring-profile walkers (nxy 1024, M 1e6 shared) and 16
+    walkers of the large single-image case (nxy 4096, M 5e6 shared): one
     gal_chi2_batch per set, its CUDA-graph replay, sequential FP32 single
     calls and sequential FP64 single calls of the same requests."""
     from paper_1709_06999_gb300 import Request, get_fft_radix, synth
@@ -730,6 +731,24 @@ def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
         w64.append(Request(o64, intensity=I.double(), **kw))
     sets["walkers"] = (w32, w64, "64 ring-profile walkers, nxy 1024, nr 8192, one M=1e6 "
                                  "observation shared, registered in Z-order", [t32] * len(w32))
+    # 16 MCMC walkers of the large single-image case: distinct models (the
+    # large image scaled per walker) and geometries, one observation shared
+    lp = synth.large_image_problem()
+    lt = [d32(a) for a in (lp.u, lp.v, lp.noise_re, lp.noise_im, lp.w)]
+    lo32 = ctx.register(*lt)
+    lo64 = ctx.register(*[t.double() for t in lt])
+    lrng = np.random.default_rng(17)
+    limg = d32(lp.image)
+    l32, l64 = [], []
+    for k in range(16):
+        img_k = limg * float(1.0 + 0.01 * k)
+        dRA, dDec = (float(x) for x in lrng.uniform(-0.1, 0.1, 2) * math.pi / 648000)
+        PA = float(lrng.uniform(0.0, math.pi))
+        l32.append(Request(lo32, image=img_k, dxy=lp.dxy, dRA=dRA, dDec=dDec, PA=PA))
+        l64.append(Request(lo64, image=img_k.double(), dxy=lp.dxy, dRA=dRA, dDec=dDec, PA=PA))
+    sets["large_walkers"] = (l32, l64, "16 walkers of the large single-image case (nxy 4096, "
+                                       "M 5e6 shared): distinct models and geometries, input order",
+                             [lt] * len(l32))
     res = {}
     for name, (a32, a64, desc, arrays) in sets.items():
         n = len(a32)
