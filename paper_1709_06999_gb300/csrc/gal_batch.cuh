@@ -120,8 +120,10 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
 }
 
 // Each request keeps the block partition of its single call (`grid` virtual
-// blocks, one partial sum each); a launch runs kGatherFold of them per block
-// in turn, so a request's window is copied by a quarter as many blocks.
+// blocks, one partial sum each); a launch of n requests runs min(n,
+// kGatherFold) of them per block in turn, so a request's window is copied by
+// a quarter as many blocks while the launch still fills the GPU (a launch of
+// one request runs its single call's grid).
 constexpr int kGatherFold = 4;
 
 template <typename T, bool SMEM, bool EDGE, bool FULL>
@@ -145,7 +147,8 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
   const int threads = gather_threads<SMEM, FULL>();
-  const int blocks = (grid + kGatherFold - 1) / kGatherFold;
+  const int fold = n < kGatherFold ? n : kGatherFold;
+  const int blocks = (grid + fold - 1) / fold;
   kern<<<dim3(blocks, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
   return cudaGetLastError();
 }
