@@ -597,23 +597,37 @@ row_fft3_ldg_kernel(const __grid_constant__ Jobs<RowJob<float>, K> jobs, const f
   C* zlo = B + RS;                  // Z[j], j < 64
   C* zhi = zlo + kRowLdgMaxKc;      // Z[M - j] at index j, j = 1..64
   const int t = threadIdx.x;
-  const Bounds bd = block_bounds(jb.rho2, jb.S, N);
-  const bool pruned = bd.Kc <= P::Nsl;
-  const bool fast = bd.Kc <= kRowLdgMaxKc;  // uniform over the request
+  auto load_row = [&](C (&x)[V], int row) {
+    // row `row` of fftshift(image): image row (row + N/2) mod N, halves swapped
+    const float* src = image + (size_t)((row + M) & (N - 1)) * N;
+#pragma unroll
+    for (int r = 0; r < V; ++r)
+      x[r] = __ldcs(reinterpret_cast<const C*>(src + ((2 * (t + r * TT) + M) & (N - 1))));
+  };
+  // the first row is in flight while the bounds (one FP64 evaluation per
+  // block) and the twiddles are read: this pass starts the evaluation, so
+  // no earlier kernel hides its prologue
+  int row = blockIdx.x;
+  C v[V];
+  if (row < N) load_row(v, row);
   // fast path: butterfly 16 blk + k of stage 1, twiddles of both stages
+  // (read before the bounds are known; replaced below for wide windows)
   const int k = t >> 3, blk = t & 7;
   C tw1[V - 1];
   C twl[8];
+#pragma unroll
+  for (int r = 1; r < V; ++r) tw1[r - 1] = __ldg(tw + 16 * r * k);  // W_256^(r k)
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int p = k + 16 * (i < 4 ? i : 8 + i);
+    const int e = (blk * p + (i < 4 ? 0 : 256 * 7 * blk)) & (M - 1);
+    twl[i] = __ldg(tw + 2 * e);  // W_2048^(blk p) W_8^(blk s)
+  }
+  const Bounds bd = block_bounds(jb.rho2, jb.S, N);
+  const bool pruned = bd.Kc <= P::Nsl;
+  const bool fast = bd.Kc <= kRowLdgMaxKc;  // uniform over the request
   C wj = mkc(0.f, 0.f);
   if (fast) {
-#pragma unroll
-    for (int r = 1; r < V; ++r) tw1[r - 1] = __ldg(tw + 16 * r * k);  // W_256^(r k)
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int p = k + 16 * (i < 4 ? i : 8 + i);
-      const int e = (blk * p + (i < 4 ? 0 : 256 * 7 * blk)) & (M - 1);
-      twl[i] = __ldg(tw + 2 * e);  // W_2048^(blk p) W_8^(blk s)
-    }
     if (t < bd.Kc) wj = __ldg(tw + t);
   } else {
     load_tw1<M, V, 2>(tw1, t, tw);
@@ -623,17 +637,7 @@ row_fft3_ldg_kernel(const __grid_constant__ Jobs<RowJob<float>, K> jobs, const f
     load_twp<M, V, 2>(twp, t, tw);
     wj = __ldg(tw + t);
   }
-  auto load_row = [&](C (&x)[V], int row) {
-    // row `row` of fftshift(image): image row (row + N/2) mod N, halves swapped
-    const float* src = image + (size_t)((row + M) & (N - 1)) * N;
-#pragma unroll
-    for (int r = 0; r < V; ++r)
-      x[r] = __ldcs(reinterpret_cast<const C*>(src + ((2 * (t + r * TT) + M) & (N - 1))));
-  };
   auto sync = [] { __syncthreads(); };
-  int row = blockIdx.x;
-  C v[V];
-  if (row < N) load_row(v, row);
   if constexpr (BEAM) grid_dep_wait();  // the beam tables
   for (; row < N; row += gridDim.x) {
     const int nrow = row + gridDim.x;
