@@ -970,14 +970,14 @@ def run_gpu(args):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize(dev)
-    # calibration (untimed): which stage dominates the step
+    # calibration (untimed): per-stage event times of a few steps (reported
+    # as stages_us; events between kernels stop the dependent launches)
     ctx.set_stage_timing(True)
     for i in range(3):
         flush_l2()
         step(i)
     cal = ctx.stage_times()
     ctx.set_stage_timing(False)
-    dom = max((1, 2, 3), key=lambda s: cal[s][0] / max(cal[s][1], 1))
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -999,16 +999,19 @@ def run_gpu(args):
     clk.end()
     clk.stop()
     gpu_launches = ctx.launch_count() - launches0
-    dom_ms, dom_n = 0.0, 0
-    ctx.set_stage_timing(True, stages=[dom])
-    for i in range(max(10, min(args.steps, 50))):
-        flush_l2()
-        step(i)
-    t = ctx.stage_times()[dom]
-    dom_ms, dom_n = t[0], t[1]
-    ctx.set_stage_timing(False)
+    # The dominant kernel: each pass's own launch time, measured the same way
+    # for all three (L2 flushed, events around that kernel alone, on separate
+    # steps after the timed region); the longest is the roofline's kernel.
     stage = {s: (0.0, 0) for s in range(4)}
-    stage[dom] = (dom_ms, dom_n)
+    for s in (1, 2, 3):
+        ctx.set_stage_timing(True, stages=[s])
+        for i in range(max(10, min(args.steps, 50))):
+            flush_l2()
+            step(i)
+        stage[s] = tuple(ctx.stage_times()[s])
+        ctx.set_stage_timing(False)
+    dom = max((1, 2, 3), key=lambda s: stage[s][0] / max(stage[s][1], 1))
+    dom_ms, dom_n = stage[dom]
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if world > 1:
@@ -1094,10 +1097,12 @@ def run_gpu(args):
                      "avg_launch_us": 1000 * avg[dom]},
         "stages_us": {STAGES[s]: round(1000 * cal[s][0] / cal[s][1], 2)
                       for s in range(4) if cal[s][1]},
-        "stages_note": "per-stage event times from 3 untimed calibration steps (each with "
-                       "about 4 us of event overhead); the dominant kernel's average launch "
-                       "time (roofline) comes from 10-50 further steps after the timed "
-                       "region, events around that kernel alone",
+        "kernel_launch_us": {STAGES[s]: round(1000 * avg[s], 2) for s in sorted(avg)},
+        "stages_note": "stages_us: per-stage event times from 3 untimed calibration steps "
+                       "(each with about 4 us of event overhead); kernel_launch_us: each "
+                       "pass timed alone on 10-50 further steps after the timed region "
+                       "(L2 flushed, events around that kernel only); the longest is the "
+                       "roofline's kernel",
         "fp64_plain": {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
                        "note": "same workload through the float64 entry point, single calls"},
         "flops": fft_equivalent(NXY, value),
