@@ -81,3 +81,28 @@ def test_row_pass_4096_branches(image, e, kc):
     ctx.check()
     obs.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_small_batches_of_the_large_case_equal_single_calls(n):
+    """A batch runs each request's gather as virtual blocks, up to four per
+    launched block but never more than the launch has requests; whatever the
+    count, every request's chi-square is its single call's, bit for bit."""
+    from paper_1709_06999_gb300 import Context, Request, synth
+    p = synth.large_image_problem(M=2_000_003, seed=9)  # 3 whole rounds, a remainder, a tail
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")  # noqa: E731
+    ctx = Context(0)
+    obs = ctx.register(dev(p.u), dev(p.v), dev(p.noise_re), dev(p.noise_im), dev(p.w))
+    img = dev(p.image)
+    rng = np.random.default_rng(n)
+    reqs = []
+    for k in range(n):
+        a, b = rng.uniform(-0.1, 0.1, 2) * math.pi / 648000
+        reqs.append(Request(obs, image=img * float(1.0 + 0.01 * k), dxy=p.dxy, dRA=float(a),
+                            dDec=float(b), PA=float(rng.uniform(0.0, math.pi))))
+    got = ctx.chi2_batch(reqs).cpu().numpy().tolist()
+    want = [ctx.chi2_image(r.image, r.dxy, obs, r.dRA, r.dDec, r.PA).item() for r in reqs]
+    assert got == want
+    ctx.check()
+    obs.close()
+    ctx.close()
