@@ -1061,7 +1061,9 @@ def run_gpu(args):
     rho = float(np.sqrt(np.max(p.u ** 2 + p.v ** 2)))
     Kc, nrw = window(rho, NXY * p.dxy, NXY)
     full = bool(opts.get("full_plane", False))
-    kernels = KERNELS_FULL if full else KERNELS
+    kernels = dict(KERNELS_FULL if full else KERNELS)
+    if "pb_fwhm" in opts and not full:  # the row pass's beam instance
+        kernels[1] = "row_fft3_ldg_kernel<1, 1>"
     if full:
         Kc = full_window_columns(Kc, NXY)
     avg = {s: (stage[s][0] / stage[s][1]) for s in (1, 2, 3) if stage[s][1]}
