@@ -106,3 +106,37 @@ def test_small_batches_of_the_large_case_equal_single_calls(n):
     ctx.check()
     obs.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("e,kc", [(60.5, 64), (200.5, 204)], ids=["Kc64", "Kc204"])
+def test_row_pass_4096_with_primary_beam(image, e, kc):
+    """The same row pass with the primary beam applied as pixels enter
+    registers (Sect. 2.1: the model times the antenna pattern, here a Gaussian
+    of FWHM about a third of the field), against the oracle; a batch of the
+    same request is bitwise its single call."""
+    from paper_1709_06999_gb300 import Context, Request
+    img, dxy = image
+    u, v, w, rng = points(e, dxy, 20011, seed=int(e) + 1)
+    fwhm = 0.35 * N * dxy
+    dRA, dDec, PA = 0.05 * math.pi / 648000, 0.02 * math.pi / 648000, 1.1
+    ref = O.sample_image(img, dxy, r32(u), r32(v), dRA, dDec, PA, pb_fwhm=fwhm)
+    plain = O.sample_image(img, dxy, r32(u), r32(v), dRA, dDec, PA)
+    assert np.max(np.abs(plain - ref)) > 1e-3 * np.max(np.abs(ref))   # the beam matters
+    re = (ref.real + rng.normal(0.0, 1.0, ref.shape) / np.sqrt(w)).astype(np.float32)
+    im = (ref.imag + rng.normal(0.0, 1.0, ref.shape) / np.sqrt(w)).astype(np.float32)
+    chi2_ref = O.chi2(ref, r32(re), r32(im), r32(w))
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")  # noqa: E731
+    ctx = Context(0)
+    gi, gu, gv = dev(img), dev(u), dev(v)
+    vis = ctx.sample_image(gi, dxy, gu, gv, dRA, dDec, PA, pb_fwhm=fwhm).double().cpu().numpy()
+    V = vis[:, 0] + 1j * vis[:, 1]
+    assert np.max(np.abs(V - ref)) / np.max(np.abs(ref)) <= TOL_VIS
+    obs = ctx.register(gu, gv, dev(re), dev(im), dev(w))
+    single = ctx.chi2_image(gi, dxy, obs, dRA, dDec, PA, pb_fwhm=fwhm).item()
+    assert abs(single - chi2_ref) <= TOL_CHI2 * chi2_ref, (single, chi2_ref)
+    batch = ctx.chi2_batch([Request(obs, image=gi, dxy=dxy, dRA=dRA, dDec=dDec, PA=PA,
+                                    pb_fwhm=fwhm)] * 2)
+    assert batch.cpu().numpy().tolist() == [single] * 2
+    ctx.check()
+    obs.close()
+    ctx.close()
