@@ -1298,8 +1298,14 @@ __device__ __forceinline__ void sample_pair(const float2* __restrict__ G, const 
     // Hermitian fold per lane, on the sign of the whole position hi + lo
     const float2 xs = add2(xh2, xl2);
     const bool n0 = xs.x < 0.f, n1 = xs.y < 0.f;
-    const float2 sg = pk(n0 ? -1.f : 1.f, n1 ? -1.f : 1.f);
-    const float2 xh = mul2(xh2, sg), xl = mul2(xl2, sg), yh = mul2(yh2, sg), yl = mul2(yl2, sg);
+    // the fold negates by flipping sign bits (integer pipe), which is what a
+    // product by -1 does to every value, NaN and zeros included
+    const unsigned f0 = n0 ? 0x80000000u : 0u, f1 = n1 ? 0x80000000u : 0u;
+    auto flip = [&](float2 a) {
+      return make_float2(__uint_as_float(__float_as_uint(a.x) ^ f0),
+                         __uint_as_float(__float_as_uint(a.y) ^ f1));
+    };
+    const float2 xh = flip(xh2), xl = flip(xl2), yh = flip(yh2), yl = flip(yl2);
     if constexpr (EDGE) {
       cell_fetch<SMEM, EDGE>(G, w, xh.x, xl.x, yh.x, yl.x, n0, A0);
       cell_fetch<SMEM, EDGE>(G, w, xh.y, xl.y, yh.y, yl.y, n1, A1);
