@@ -1136,12 +1136,20 @@ __device__ __forceinline__ int floor_fma(float x, float& fl) {
 
 using Pair2Const = GatherT<float>;  // the broadcast pairs live in the kernel parameters
 
+// -a for both lanes, by flipping the sign bits (integer pipe): exactly the
+// product by -1, which frees the FMA pipe the float-float steps load
+__device__ __forceinline__ float2 neg2(float2 a) {
+  return make_float2(__uint_as_float(__float_as_uint(a.x) ^ 0x80000000u),
+                     __uint_as_float(__float_as_uint(a.y) ^ 0x80000000u));
+}
+
 // x * c exactly as hi + lo for c = ch + cl: hi = x ch, lo = (x ch - hi) + x cl.
-// nch = -ch gives -hi without a negation instruction.
+// (nch = -ch is no longer needed: -hi is hi with its sign flipped, which is
+// x (-ch) exactly.)
 __device__ __forceinline__ float2 prod2(float2 x, float2 ch, float2 nch, float2 cl, float2& lo) {
+  (void)nch;
   const float2 hi = mul2(x, ch);
-  const float2 nhi = mul2(x, nch);
-  lo = fma2(x, cl, fma2(x, ch, nhi));
+  lo = fma2(x, cl, fma2(x, ch, neg2(hi)));
   return hi;
 }
 
@@ -1239,8 +1247,8 @@ __device__ __forceinline__ void cell_pair_pruned(const float2* __restrict__ G, c
 __device__ __forceinline__ float2 phase_turns2(float2 U, float2 Vv, float2 PXh, float2 PXl,
                                                float2 PYh, float2 PYl, float2 m1) {
   const float2 pa = mul2(U, PXh), pb = mul2(Vv, PYh);
-  const float2 pe1 = fma2(U, PXl, fma2(U, PXh, mul2(pa, m1)));
-  const float2 pe2 = fma2(Vv, PYl, fma2(Vv, PYh, mul2(pb, m1)));
+  const float2 pe1 = fma2(U, PXl, fma2(U, PXh, neg2(pa)));
+  const float2 pe2 = fma2(Vv, PYl, fma2(Vv, PYh, neg2(pb)));
   const float2 ra = fma2(rint_fma2(pa), m1, pa);  // exact, |ra| <= 1
   const float2 rb = fma2(rint_fma2(pb), m1, pb);
   const float2 f = add2(add2(ra, rb), add2(pe1, pe2));
