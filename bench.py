@@ -683,6 +683,15 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200)
     return res
 
 
+def launch_shape(ctx, reqs):
+    """The float32 launch shape the context keeps for this batch (tuned by its
+    first call): every request here runs in the batched kernels."""
+    import torch
+    (rb, jobs, fold), kept = ctx.batch_shape(torch.float32, len(reqs), max(r.nxy for r in reqs))
+    return {"row_blocks_per_sm": rb, "requests_per_launch": jobs, "gather_fold": fold,
+            "tuned": kept}
+
+
 def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
     """Spectral cube (128 Keplerian channels, nxy in {512, 1024, 2048}, M_c in
     [1e5, 2e6]), 64 ring-profile walkers (nxy 1024, M 1e6 shared) and 16
@@ -795,6 +804,7 @@ def measure_batched(torch, ctx, dev, flush, reps=3, n_oracle=3):
             "oracle_checked_requests": n_oracle,
             "fft_plans": {str(nx): list(get_fft_radix(dev.index or 0, torch.float32, nx))
                           for nx in sorted({int(r.nxy) for r in a32})},
+            "launch_shape": launch_shape(ctx, a32),
             "roofline": res_roof,
         }
         g.close()

@@ -376,8 +376,8 @@ typedef struct gal_request {
  * Launch shapes: the first batch of each (precision, request count, largest
  * side) is run once per candidate shape, timed with events on `stream`
  * (synchronising it) and the fastest shape is kept for the context; results do
- * not depend on the shape.  gal_set_batch_tuning(ctx, 0) turns this off
- * (default shape).  The batch workspace (about nxy*Kc*2 complex values per
+ * not depend on the shape (gal_set_batch_shape below lists the candidates).
+ * gal_set_batch_tuning(ctx, 0) turns this off (default shape).  The batch workspace (about nxy*Kc*2 complex values per
  * request) grows on first use; like every call on a context, batches on
  * different streams must not overlap.
  * Errors: GAL_E_INVAL if any request is invalid (nothing is launched then). */
@@ -385,6 +385,36 @@ int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_ou
 /* enable = 0 turns off the context's tuning: launch shapes of batches and the
  * FFT plans of sides it is first to use (which then take the default). */
 int gal_set_batch_tuning(gal_ctx* ctx, int enable);
+
+/* Launch shapes of batches (an implementation choice: the paper evaluates one
+ * model per call, Sect. 4).  A shape is three integers:
+ *   row_blocks       persistent row-pass blocks per SM for each group of
+ *                    requests (1 .. 8);
+ *   jobs_per_launch  requests per launch of each pass (1 .. 32);
+ *   gather_fold      how many of a request's single-call gather blocks one
+ *                    launched block runs in turn (1 .. 8; a launch of m
+ *                    requests uses min(m, gather_fold)), so that its window
+ *                    is copied into shared memory that many times fewer.
+ * The context keeps one shape per key (real_bytes 4 or 8; n, the number of
+ * the batch's requests of that precision that run in the batched kernels;
+ * max_nxy, the largest side among them).  The first batch of a key tunes it
+ * when tuning is on: the six pairs (row_blocks, jobs_per_launch) of (1, 32),
+ * (2, 32), (4, 32), (1, 8), (2, 8), (4, 16) at fold 4, then folds 1, 2 and 8
+ * with the fastest pair, each run twice on the batch's stream (the first run
+ * warms up); the fastest is kept.  Without tuning (off, or the stream being
+ * captured) a key takes the default (1, 32, 4).  Results are bitwise the same
+ * for every shape.
+ *   gal_set_batch_shape  fixes the shape of a key (before or after tuning);
+ *                        GAL_E_INVAL for a value outside the ranges above or
+ *                        max_nxy not a power of two in 4 .. 8192.
+ *   gal_get_batch_shape  writes the shape the next batch of that key will use
+ *                        to shape_out3 = {row_blocks, jobs_per_launch,
+ *                        gather_fold}: the kept one, or the default when none
+ *                        is kept yet; *cached (may be NULL) = 1 if one is kept. */
+int gal_set_batch_shape(gal_ctx* ctx, int real_bytes, int n, int max_nxy, int row_blocks,
+                        int jobs_per_launch, int gather_fold);
+int gal_get_batch_shape(const gal_ctx* ctx, int real_bytes, int n, int max_nxy, int* shape_out3,
+                        int* cached);
 
 /* FFT plans (an implementation choice; the paper's transform is any FFT,
  * Sect. 4).  The row and column passes of a float32 image of side 32 .. 512

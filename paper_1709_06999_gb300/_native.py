@@ -99,6 +99,8 @@ _SIGNATURES.update({
     "gal_server_destroy": (None, [P]),
     "gal_chi2_batch": (I32, [P, ct.POINTER(GalRequest), I32, P, P]),
     "gal_set_batch_tuning": (I32, [P, I32]),
+    "gal_set_batch_shape": (I32, [P, I32, I32, I32, I32, I32, I32]),
+    "gal_get_batch_shape": (I32, [P, I32, I32, I32, ct.POINTER(I32), ct.POINTER(I32)]),
     "gal_set_fft_radix": (I32, [I32, I32, I32, I32, I32]),
     "gal_get_fft_radix": (I32, [I32, I32, I32, ct.POINTER(I32), ct.POINTER(I32)]),
     "gal_chi2_batch_capture": (I32, [P, ct.POINTER(GalRequest), I32, P, P, ct.POINTER(P)]),

@@ -467,6 +467,24 @@ class Context:
     def set_batch_tuning(self, enable: bool):
         _check(self.handle, self.lib.gal_set_batch_tuning(self.handle, int(enable)))
 
+    def set_batch_shape(self, dtype, n: int, max_nxy: int, row_blocks: int,
+                        jobs_per_launch: int, gather_fold: int):
+        """Fix the launch shape of batches with n requests of this precision
+        in the batched kernels, largest side max_nxy (gal_set_batch_shape)."""
+        _check(self.handle, self.lib.gal_set_batch_shape(
+            self.handle, _real_bytes(dtype), int(n), int(max_nxy), int(row_blocks),
+            int(jobs_per_launch), int(gather_fold)))
+
+    def batch_shape(self, dtype, n: int, max_nxy: int):
+        """((row_blocks, jobs_per_launch, gather_fold), kept) for that batch
+        key: the shape its next batch uses, and whether it was tuned or set
+        (gal_get_batch_shape)."""
+        sh = (ct.c_int * 3)()
+        kept = ct.c_int()
+        _check(self.handle, self.lib.gal_get_batch_shape(self.handle, _real_bytes(dtype), int(n),
+                                                         int(max_nxy), sh, ct.byref(kept)))
+        return (sh[0], sh[1], sh[2]), bool(kept.value)
+
     def capture_batch(self, requests, out=None) -> BatchGraph:
         if out is None:
             out = torch.empty(len(requests), dtype=torch.float64, device=self.device)

@@ -1051,7 +1051,7 @@ int enqueue_items(gal_ctx* ctx, const std::vector<gal::BatchItem>& items,
   return GAL_OK;
 }
 
-constexpr gal::BatchShape kDefaultShape{1, gal::kBatchJobs};
+constexpr gal::BatchShape kDefaultShape{1, gal::kBatchJobs, gal::kGatherFold};
 
 // Everything of a planned batch except the batched passes' shapes.
 int enqueue_rest(gal_ctx* ctx, const gal_request* reqs, const BatchPlan& pl, double* chi2_out,
@@ -1075,8 +1075,11 @@ int enqueue_rest(gal_ctx* ctx, const gal_request* reqs, const BatchPlan& pl, dou
   return GAL_OK;
 }
 
-// Launch shape for precision p of this plan: cached, or tuned now by timing
-// every candidate on the stream (results are identical for all of them).
+// Launch shape for precision p of this plan: cached (tuned earlier or set by
+// gal_set_batch_shape), or tuned now by timing candidates on the stream
+// (results are identical for all of them).  Two stages: the row-pass blocks
+// and requests per launch at the default gather fold, then the gather fold
+// with the pair that won.
 int batch_shape(gal_ctx* ctx, const BatchPlan& pl, int p, cudaStream_t st, gal::BatchShape* out) {
   *out = kDefaultShape;
   const int n = (int)pl.items[p].size();
@@ -1090,7 +1093,9 @@ int batch_shape(gal_ctx* ctx, const BatchPlan& pl, int p, cudaStream_t st, gal::
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   GAL_CUDA(ctx, cudaStreamIsCapturing(st, &cap));
   if (!ctx->batch_tuning || cap != cudaStreamCaptureStatusNone) return GAL_OK;
-  const gal::BatchShape cands[] = {{1, 32}, {2, 32}, {4, 32}, {1, 8}, {2, 8}, {4, 16}};
+  constexpr int F = gal::kGatherFold;
+  const gal::BatchShape stage1[] = {{1, 32, F}, {2, 32, F}, {4, 32, F},
+                                    {1, 8, F},  {2, 8, F},  {4, 16, F}};
   cudaEvent_t a, b;
   GAL_CUDA(ctx, cudaEventCreate(&a));
   GAL_CUDA(ctx, cudaEventCreate(&b));
@@ -1099,7 +1104,7 @@ int batch_shape(gal_ctx* ctx, const BatchPlan& pl, int p, cudaStream_t st, gal::
   const int saved_timing = ctx->timing;
   ctx->timing = 0;
   int status = GAL_OK;
-  for (const auto& c : cands) {
+  auto time_one = [&](const gal::BatchShape& c) {
     float ms = 1e30f;
     for (int rep = 0; rep < 2 && status == GAL_OK; ++rep) {  // first run warms up
       cudaEventRecord(a, st);
@@ -1112,10 +1117,23 @@ int batch_shape(gal_ctx* ctx, const BatchPlan& pl, int p, cudaStream_t st, gal::
         ms = std::min(ms, t);
       }
     }
-    if (status != GAL_OK) break;
-    if (ms < best) {
+    if (status == GAL_OK && ms < best) {
       best = ms;
       pick = c;
+    }
+  };
+  for (const auto& c : stage1) {
+    if (status != GAL_OK) break;
+    time_one(c);
+  }
+  // the gather fold matters only when a launch holds more than one request
+  const int per_launch = std::min(n, pick.jobs_per_launch);
+  if (per_launch > 1) {
+    const gal::BatchShape pair = pick;
+    for (int fold : {1, 2, 8}) {
+      if (status != GAL_OK) break;
+      if (fold > per_launch && fold != 1) continue;  // same launch as min(n, fold)
+      time_one(gal::BatchShape{pair.row_blocks, pair.jobs_per_launch, fold});
     }
   }
   ctx->timing = saved_timing;
@@ -1379,6 +1397,33 @@ int gal_chi2_batch(gal_ctx* ctx, const gal_request* reqs, int n, double* chi2_ou
 int gal_set_batch_tuning(gal_ctx* ctx, int enable) {
   if (!ctx) return GAL_E_INVAL;
   ctx->batch_tuning = enable != 0;
+  return GAL_OK;
+}
+
+int gal_set_batch_shape(gal_ctx* ctx, int real_bytes, int n, int max_nxy, int row_blocks,
+                        int jobs_per_launch, int gather_fold) {
+  if (!ctx || (real_bytes != 4 && real_bytes != 8) || n < 1 || !pow2_size(max_nxy))
+    return GAL_E_INVAL;
+  if (row_blocks < 1 || row_blocks > 8 || jobs_per_launch < 1 ||
+      jobs_per_launch > gal::kBatchJobs || gather_fold < 1 || gather_fold > gal::kMaxGatherFold)
+    return GAL_E_INVAL;
+  ctx->batch_shapes[std::make_tuple(real_bytes == 8 ? 1 : 0, n, max_nxy)] =
+      gal::BatchShape{row_blocks, jobs_per_launch, gather_fold};
+  return GAL_OK;
+}
+
+int gal_get_batch_shape(const gal_ctx* ctx, int real_bytes, int n, int max_nxy, int* shape_out3,
+                        int* cached) {
+  if (!ctx || !shape_out3 || (real_bytes != 4 && real_bytes != 8) || n < 1 || max_nxy < 1)
+    return GAL_E_INVAL;
+  gal::BatchShape sh = kDefaultShape;
+  auto it = ctx->batch_shapes.find(std::make_tuple(real_bytes == 8 ? 1 : 0, n, max_nxy));
+  const bool have = it != ctx->batch_shapes.end();
+  if (have) sh = it->second;
+  shape_out3[0] = sh.row_blocks;
+  shape_out3[1] = sh.jobs_per_launch;
+  shape_out3[2] = sh.gather_fold;
+  if (cached) *cached = have ? 1 : 0;
   return GAL_OK;
 }
 

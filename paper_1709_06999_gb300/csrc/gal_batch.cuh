@@ -120,14 +120,14 @@ cudaError_t cols(const BatchItem* it, const int* idx, int n, const void* tw, cud
 }
 
 // Each request keeps the block partition of its single call (`grid` virtual
-// blocks, one partial sum each); a launch of n requests runs min(n,
-// kGatherFold) of them per block in turn, so a request's window is copied by
-// a quarter as many blocks while the launch still fills the GPU (a launch of
-// one request runs its single call's grid).
-constexpr int kGatherFold = 4;
-
+// blocks, one partial sum each); a launch of n requests runs min(n, fold) of
+// them per block in turn (fold from the launch shape, kGatherFold by
+// default), so a request's window is copied by that many times fewer blocks
+// while the launch still fills the GPU (a launch of one request runs its
+// single call's grid).
 template <typename T, bool SMEM, bool EDGE, bool FULL>
-cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStream_t st) {
+cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, int fold_max,
+                   cudaStream_t st) {
   using C = cplx_t<T>;
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   Jobs<GatherJob<T>, kBatchJobs> jb{};
@@ -147,7 +147,9 @@ cudaError_t gather(const BatchItem* it, const int* idx, int n, int grid, cudaStr
   const cudaError_t e = ensure_smem_attr<kern>(smem);
   if (e) return e;
   const int threads = gather_threads<SMEM, FULL>();
-  const int fold = n < kGatherFold ? n : kGatherFold;
+  if (fold_max < 1) fold_max = 1;
+  if (fold_max > kMaxGatherFold) fold_max = kMaxGatherFold;
+  const int fold = n < fold_max ? n : fold_max;
   const int blocks = (grid + fold - 1) / fold;
   kern<<<dim3(blocks, n), threads, smem, st>>>(jb, (int)(smem / sizeof(C)), MultiArg<T, false>{});
   return cudaGetLastError();
@@ -198,7 +200,7 @@ cudaError_t for_chunks(const BatchItem* it, int n, const BatchShape& sh, Pick&& 
 
 template <typename T>
 cudaError_t BatchLaunch<T>::beams(const BatchItem* it, int n, int* launches, cudaStream_t st) {
-  const BatchShape sh{1, kBatchJobs};
+  const BatchShape sh{1, kBatchJobs, kGatherFold};
   auto pick = [](const BatchItem& b) { return b.beam != nullptr; };
   auto key = [](const BatchItem&) { return 0; };
   return batch::for_chunks(it, n, sh, pick, key, [&](const int* idx, int m, const BatchItem&) {
@@ -295,11 +297,12 @@ cudaError_t BatchLaunch<T>::gather(const BatchItem* it, int n, const BatchShape&
     cudaError_t e;
     auto go = [&](auto full_c) {
       constexpr bool F = decltype(full_c)::value;
+      const int fold = sh.gather_fold;
       if (b0.wbytes)
-        return b0.edge ? batch::gather<T, true, true, F>(it, idx, m, b0.grid, st)
-                       : batch::gather<T, true, false, F>(it, idx, m, b0.grid, st);
-      return b0.edge ? batch::gather<T, false, true, F>(it, idx, m, b0.grid, st)
-                     : batch::gather<T, false, false, F>(it, idx, m, b0.grid, st);
+        return b0.edge ? batch::gather<T, true, true, F>(it, idx, m, b0.grid, fold, st)
+                       : batch::gather<T, true, false, F>(it, idx, m, b0.grid, fold, st);
+      return b0.edge ? batch::gather<T, false, true, F>(it, idx, m, b0.grid, fold, st)
+                     : batch::gather<T, false, false, F>(it, idx, m, b0.grid, fold, st);
     };
     e = b0.full ? go(std::true_type{}) : go(std::false_type{});
     if (!e) ++*launches;

@@ -156,7 +156,10 @@ struct BatchItem {
 struct BatchShape {
   int row_blocks;       // persistent row-pass blocks per SM and request group (1, 2, 4)
   int jobs_per_launch;  // requests per launch (<= kBatchJobs)
+  int gather_fold;      // a request's single-call gather blocks run per launched block (1..8)
 };
+constexpr int kGatherFold = 4;     // default gather fold
+constexpr int kMaxGatherFold = 8;  // largest fold a shape may ask for
 
 // Batched passes: each launch covers up to jobs_per_launch requests of one
 // transform length (grid row y = request).  `tw[lg]` is the twiddle table of

@@ -150,6 +150,48 @@ def test_tuning_does_not_change_results():
     assert torch.equal(a, b) and torch.equal(b, c)
 
 
+def test_launch_shapes_do_not_change_results():
+    """Every launch shape (row-pass blocks per SM, requests per launch,
+    gather fold) gives the single calls' results bit for bit, on windows
+    staged in shared memory (sides 32..128) and read through L2 (side 256);
+    a shape set for a batch key is read back and used."""
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float32, seed=11, n_img=12, n_prof=4)
+    want = torch.stack([single(ctx, r) for r in reqs])
+    n, nmax = len(reqs), max(r.nxy for r in reqs)
+    assert ctx.batch_shape(torch.float32, n, nmax) == ((1, 32, 4), False)  # the default
+    for shape in [(1, 32, 1), (2, 8, 2), (4, 16, 8), (1, 3, 4), (8, 1, 8), (2, 32, 3)]:
+        ctx.set_batch_shape(torch.float32, n, nmax, *shape)
+        assert ctx.batch_shape(torch.float32, n, nmax) == (shape, True)
+        got = ctx.chi2_batch(reqs)
+        assert torch.equal(got, want), shape
+
+
+def test_tuner_keeps_a_candidate_shape():
+    ctx = Context(0)
+    reqs, keep = mixed_requests(ctx, torch.float64, seed=13, n_img=5, n_prof=3)
+    n, nmax = len(reqs), max(r.nxy for r in reqs)
+    got = ctx.chi2_batch(reqs)                        # tunes this key
+    (rb, jobs, fold), kept = ctx.batch_shape(torch.float64, n, nmax)
+    assert kept
+    assert (rb, jobs) in {(1, 32), (2, 32), (4, 32), (1, 8), (2, 8), (4, 16)}
+    assert fold in (1, 2, 4, 8)
+    assert ctx.batch_shape(torch.float32, n, nmax)[1] is False   # other precision untouched
+    assert torch.equal(got, torch.stack([single(ctx, r) for r in reqs]))
+
+
+def test_batch_shape_validation():
+    ctx = Context(0)
+    for bad in ((torch.float32, 0, 256, 1, 32, 4), (torch.float32, 4, 300, 1, 32, 4),
+                (torch.float32, 4, 256, 0, 32, 4), (torch.float32, 4, 256, 9, 32, 4),
+                (torch.float32, 4, 256, 1, 33, 4), (torch.float32, 4, 256, 1, 0, 4),
+                (torch.float32, 4, 256, 1, 32, 0), (torch.float32, 4, 256, 1, 32, 9)):
+        with pytest.raises(GalError):
+            ctx.set_batch_shape(*bad)
+    with pytest.raises(ValueError):
+        ctx.set_batch_shape(torch.int32, 4, 256, 1, 32, 4)
+
+
 def test_graph_replay_update_and_regrowth():
     ctx = Context(0)
     reqs, keep = mixed_requests(ctx, torch.float32, seed=7, n_img=5, n_prof=3)
