@@ -354,6 +354,37 @@ def oracle_eval_threads(p, re, im, pool, nthreads: int):
     return math.fsum(pool.map(part, range(nthreads)))
 
 
+def oracle_chi2_sharded(p, re, im, dRA, dDec, PA, pool, nthreads: int, pb_fwhm: float = 0.0,
+                        full_plane: bool = False, copies=None):
+    """The FP64 oracle's chi-square of one evaluation of the workload p (its
+    float32-rounded inputs, observed data re, im) at the geometry (dRA, dDec,
+    PA): the oracle's spectrum of the image (times its primary beam when
+    pb_fwhm > 0, the complex-to-complex one for full_plane) computed once,
+    then its sampling on nthreads contiguous shares of the points in a thread
+    pool -- summed over the copies (amp, dRA_k, dDec_k) of a multi-source
+    model when given, the linear sum that sample_image_multi forms -- and its
+    chi-square of each share, the shares' exactly rounded sums added with
+    math.fsum."""
+    import oracle
+    n = p.image.shape[0]
+    img = p.image
+    if pb_fwhm > 0.0:
+        img = img * oracle.primary_beam(n, p.dxy, pb_fwhm, dRA, dDec, PA)
+    G = oracle.full_spectrum(img) if full_plane else oracle.half_spectrum(img)
+    sample = oracle.sample_full_spectrum if full_plane else oracle.sample_spectrum
+    offsets = copies if copies is not None else [(1.0, dRA, dDec)]
+    b = np.linspace(0, p.u.size, nthreads + 1).astype(np.int64)
+
+    def part(k):
+        s = slice(int(b[k]), int(b[k + 1]))
+        vis = 0.0
+        for a, x, y in offsets:
+            vis = vis + a * sample(G, n, p.dxy, p.u[s], p.v[s], x, y, PA)
+        return oracle.chi2(vis, re[s], im[s], p.w[s])
+
+    return math.fsum(pool.map(part, range(nthreads)))
+
+
 def cpu_baseline(p, re, im, evals: int):
     """The FP64 oracle timed on the host cores on full evaluations of the
     workload: single-threaded (numpy as it stands) and on all usable cores
@@ -577,10 +608,14 @@ def _single(ctx, r, out=None):
                             r.PA, out=out, pb_fwhm=r.pb_fwhm)
 
 
-def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=200):
+def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=200,
+                  oracle_chi2=None):
     """chi2_image of the same workload with a primary beam, through the
     full-plane spectrum, and both: L2 flushed before every step, each step
-    bracketed by events, plus per-stage times from three calibration steps."""
+    bracketed by events, plus per-stage times from three calibration steps.
+    oracle_chi2(dRA, dDec, PA, pb_fwhm=..., full_plane=...), when given, is
+    the FP64 oracle's chi-square of that evaluation: each variant's result at
+    the first geometry is stated against it."""
     variants = {k: v for k, v in VARIANTS.items() if k != "plain"}
     stream = torch.cuda.current_stream(dev)
     res = {}
@@ -608,18 +643,26 @@ def measure_plane(torch, ctx, dev, img, obs, dxy, params, flush_l2, out, steps=2
                      "full_plane": bool(kw.get("full_plane", False)),
                      "stages_us_per_step": {STAGES[s]: round(1000 * cal[s][0] / 3, 2)
                                             for s in range(4) if cal[s][1]}}
+        if oracle_chi2 is not None:
+            got = ctx.chi2_image(img, dxy, obs, *params[0], out=out, **kw).item()
+            ref = oracle_chi2(*params[0], pb_fwhm=kw.get("pb_fwhm", 0.0),
+                              full_plane=bool(kw.get("full_plane", False)))
+            res[name]["chi2_rel_err_vs_oracle"] = abs(got - ref) / abs(ref)
     res["note"] = ("same workload and timing as the headline step; per-stage times are sums "
                    "per step over 3 calibration steps, each launch with about 4 us of event "
                    "overhead; the beam-table launch belongs to the row stage")
     return res
 
 
-def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200):
+def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200,
+                 oracle_chi2=None):
     """The widened paths at the headline workload: multi-source chi2 (K copies
     of the model, one FFT, K phase terms per point; L2 flushed before every
     step, each step event-timed), registration from baselines in metres with
     one frequency per visibility, and get_image_size on the same coverage (both
-    return to the host, so they are wall-clock timed per call)."""
+    return to the host, so they are wall-clock timed per call).  oracle_chi2,
+    when given, states each multi-source result at the first position angle
+    against the FP64 oracle (its copies= argument)."""
     stream = torch.cuda.current_stream(dev)
     rng = np.random.default_rng(31)
     arc = math.pi / 648000
@@ -654,6 +697,11 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200)
             "value": 1000.0 / ms, "unit": UNIT, "ms_per_step": ms, "sources": K,
             "stages_us_per_step": {STAGES[s]: round(1000 * cal[s][0] / 3, 2)
                                    for s in range(4) if cal[s][1]}}
+        if oracle_chi2 is not None:
+            PA0 = params[0][2]
+            got = ctx.chi2_image_multi(img, p.dxy, obs, dra, ddec, amp, PA0, out=out).item()
+            ref = oracle_chi2(0.0, 0.0, PA0, copies=list(zip(amp, dra, ddec)))
+            res[f"multi_source_K{K}"]["chi2_rel_err_vs_oracle"] = abs(got - ref) / abs(ref)
     # one frequency per visibility around 100 GHz (the coverage's 93 channels
     # span +-3.75 %), baselines in metres = u c / nu
     M = p.u.size
@@ -1129,10 +1177,22 @@ def run_gpu(args):
         line["accuracy"] = accuracy
     if world == 1 and not args.no_extras:
         extras = set(args.extras.split(","))
+        check, pool = None, None
+        if not args.no_accuracy:
+            from concurrent.futures import ThreadPoolExecutor
+            nthr = max(1, host_info()["usable_cpus"] or 1)
+            pool = ThreadPoolExecutor(nthr)
+
+            def check(dRA, dDec, PA, **kw):
+                return oracle_chi2_sharded(p, re_h, im_h, dRA, dDec, PA, pool, nthr, **kw)
         if "plane" in extras:
-            line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out)
+            line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out,
+                                          oracle_chi2=check)
         if "next" in extras:
-            line["next"] = measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out)
+            line["next"] = measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out,
+                                        oracle_chi2=check)
+        if pool is not None:
+            pool.shutdown()
         if "batched" in extras:
             line["batched"] = measure_batched(torch, ctx, dev, flush_l2)
         if "serving" in extras:

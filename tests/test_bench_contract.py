@@ -102,3 +102,34 @@ def test_fft_equivalent():
     f = bench.fft_equivalent(4096, 1000.0)
     assert abs(f["fft_gflop_per_eval"] - 2.5 * 4096 ** 2 * 24 / 1e9) < 1e-12
     assert abs(f["fft_equivalent_tflop_per_s"] - f["fft_gflop_per_eval"]) < 1e-12
+
+
+def test_sharded_oracle_chi2_is_the_oracle():
+    """The bench states the beam, full-plane and multi-source results against
+    oracle_chi2_sharded: it must be the oracle's own chi-square of that
+    evaluation (chi2_image with pb_fwhm / full_plane, chi2_image_multi), the
+    sharding changing only the last bits of the sum."""
+    import math
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_1709_06999_gb300 import synth
+    p = synth.small_image_problem(nxy=64, M=5003, seed=3)
+    re, im = p.noise_re + 0.1, p.noise_im - 0.2
+    fwhm = 0.4 * 64 * p.dxy
+    with ThreadPoolExecutor(3) as pool:
+        for kw in ({}, {"pb_fwhm": fwhm}, {"full_plane": True},
+                   {"pb_fwhm": fwhm, "full_plane": True}):
+            got = bench.oracle_chi2_sharded(p, re, im, p.dRA, p.dDec, p.PA, pool, 3, **kw)
+            ref = oracle.chi2_image(p.image, p.dxy, p.u, p.v, re, im, p.w, p.dRA, p.dDec, p.PA,
+                                    **kw)
+            assert math.isclose(got, ref, rel_tol=1e-14), (kw, got, ref)
+        copies = [(0.7, 1e-7, -2e-7), (0.3, -3e-7, 1e-7), (1.1, 0.0, 2e-7)]
+        got = bench.oracle_chi2_sharded(p, re, im, 0.0, 0.0, p.PA, pool, 3, copies=copies)
+        amp, dra, ddec = (list(c) for c in zip(*copies))
+        ref = oracle.chi2_image_multi(p.image, p.dxy, p.u, p.v, re, im, p.w, dra, ddec, amp, p.PA)
+        assert math.isclose(got, ref, rel_tol=1e-14), (got, ref)
+        # a different beam or offset moves it: the check is not blind
+        off = bench.oracle_chi2_sharded(p, re, im, p.dRA, p.dDec, p.PA, pool, 3,
+                                        pb_fwhm=0.5 * fwhm)
+        assert not math.isclose(off, ref, rel_tol=1e-6)
