@@ -662,7 +662,9 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200,
     one frequency per visibility, and get_image_size on the same coverage (both
     return to the host, so they are wall-clock timed per call).  oracle_chi2,
     when given, states each multi-source result at the first position angle
-    against the FP64 oracle (its copies= argument)."""
+    against the FP64 oracle (its copies= argument), the chi-square of the
+    observation registered from metres against the oracle's at its own
+    wavelengths (problem=), and get_image_size against oracle.image_size."""
     stream = torch.cuda.current_stream(dev)
     rng = np.random.default_rng(31)
     arc = math.pi / 648000
@@ -720,6 +722,23 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200,
         "ms_per_registration": ms_f, "points": M,
         "note": "u_m, v_m, nu (f32) -> u, v in wavelengths (FP64 product, rounded once), then "
                 "the uv extent and its read-back; includes the handle's allocation"}
+    if oracle_chi2 is not None:
+        # chi2 of the observation registered from metres and frequencies,
+        # against the oracle's chi2 at its own wavelengths (uv_from_frequency
+        # of the same float32 values, rounded to float32 as the kernel stores
+        # them)
+        import copy
+        import oracle
+        obs_f = ctx.register_freq(u_m, v_m, nu_d, *rest)
+        got = ctx.chi2_image(img, p.dxy, obs_f, *params[0], out=out).item()
+        obs_f.close()
+        uw, vw = oracle.uv_from_frequency(u_m.double().cpu().numpy(), v_m.double().cpu().numpy(),
+                                          nu_d.double().cpu().numpy())
+        pf = copy.copy(p)
+        pf.u = uw.astype(np.float32).astype(np.float64)
+        pf.v = vw.astype(np.float32).astype(np.float64)
+        ref = oracle_chi2(*params[0], problem=pf)
+        res["freq_registration"]["chi2_rel_err_vs_oracle"] = abs(got - ref) / abs(ref)
     u_d, v_d = obs._tensors[0], obs._tensors[1]
     ctx.get_image_size(u_d, v_d)
     t0 = time.perf_counter()
@@ -728,6 +747,10 @@ def measure_next(torch, ctx, dev, img, obs, p, params, flush_l2, out, steps=200,
     res["image_size"] = {"ms_per_call": 1000.0 * (time.perf_counter() - t0) / reps, "nxy": nxy,
                          "dxy_arcsec": dxy / arc, "points": M,
                          "note": "criterion (iia) of Sect. 3.3 on the 5e6-point coverage"}
+    if oracle_chi2 is not None:
+        import oracle
+        n_ref, dxy_ref = oracle.image_size(p.u, p.v)
+        res["image_size"]["oracle"] = {"nxy": int(n_ref), "dxy_rel_err": abs(dxy - dxy_ref) / dxy_ref}
     return res
 
 
@@ -1183,8 +1206,9 @@ def run_gpu(args):
             nthr = max(1, host_info()["usable_cpus"] or 1)
             pool = ThreadPoolExecutor(nthr)
 
-            def check(dRA, dDec, PA, **kw):
-                return oracle_chi2_sharded(p, re_h, im_h, dRA, dDec, PA, pool, nthr, **kw)
+            def check(dRA, dDec, PA, problem=None, **kw):
+                return oracle_chi2_sharded(p if problem is None else problem, re_h, im_h, dRA,
+                                           dDec, PA, pool, nthr, **kw)
         if "plane" in extras:
             line["plane"] = measure_plane(torch, ctx, dev, img, obs, p.dxy, params, flush_l2, out,
                                           oracle_chi2=check)
