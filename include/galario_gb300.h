@@ -405,8 +405,9 @@ int gal_set_batch_tuning(gal_ctx* ctx, int enable);
  * captured) a key takes the default (1, 32, 4).  Results are bitwise the same
  * for every shape.
  *   gal_set_batch_shape  fixes the shape of a key (before or after tuning);
- *                        GAL_E_INVAL for a value outside the ranges above or
- *                        max_nxy not a power of two in 4 .. 8192.
+ *                        GAL_E_INVAL for a NULL context, real_bytes other
+ *                        than 4 or 8, n < 1, a value outside the ranges
+ *                        above or max_nxy not a power of two in 4 .. 8192.
  *   gal_get_batch_shape  writes the shape the next batch of that key will use
  *                        to shape_out3 = {row_blocks, jobs_per_launch,
  *                        gather_fold}: the kept one, or the default when none
