@@ -598,11 +598,14 @@ row_fft3_ldg_kernel(const __grid_constant__ Jobs<RowJob<float>, K> jobs, const f
   C* zhi = zlo + kRowLdgMaxKc;      // Z[M - j] at index j, j = 1..64
   const int t = threadIdx.x;
   auto load_row = [&](C (&x)[V], int row) {
-    // row `row` of fftshift(image): image row (row + N/2) mod N, halves swapped
-    const float* src = image + (size_t)((row + M) & (N - 1)) * N;
+    // row `row` of fftshift(image): image row (row + N/2) mod N, halves
+    // swapped: pixel pairs t + r TT of the shifted row are pairs M/2 + t + r TT
+    // of the image row for r < V/2 and t + (r - V/2) TT after the wrap
+    // (TT = M/8 pairs, so 2 (t + r TT) + M < N exactly when r < V/2)
+    const C* src = reinterpret_cast<const C*>(image + (size_t)((row + M) & (N - 1)) * N) + t;
 #pragma unroll
     for (int r = 0; r < V; ++r)
-      x[r] = __ldcs(reinterpret_cast<const C*>(src + ((2 * (t + r * TT) + M) & (N - 1))));
+      x[r] = __ldcs(r < V / 2 ? src + M / 2 + r * TT : src + (r - V / 2) * TT);
   };
   // the first row is in flight while the bounds (one FP64 evaluation per
   // block) and the twiddles are read: this pass starts the evaluation, so
